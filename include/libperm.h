@@ -1,0 +1,166 @@
+/*
+ * libperm.h -- C ABI of libperm: matrix permanents on one GB300 (sm_103a).
+ *
+ * The permanent of an n x n matrix A is per(A) = sum over all permutations s of
+ * {0..n-1} of prod_i a[i][s(i)]  (Su & Zheng, arXiv:1802.02779, Section 3.1,
+ * Eq. (1)).  It is the quantity a boson-sampling amplitude is proportional to
+ * (Section 2).  libperm evaluates it with two GPU methods:
+ *
+ *  - Store-zechin (Section 4): per(A) is developed along a row without signs
+ *    (Section 3.1, property 4); every sub-permanent
+ *        T_k[S] = per(rows 0..k-1, columns S),  |S| = k,
+ *    is computed once, as  T_k[S] = sum_{j in S, ascending} a[k-1][j] * T_{k-1}[S \ {j}],
+ *    stored, and reused by every larger minor that contains it.  This is the
+ *    primary method.
+ *  - Ryser's inclusion-exclusion formula (Section 3.3, Eqs. (2)-(4)) walked in
+ *    Gray-code order.  It needs no tables and is the fallback when the
+ *    Store-zechin tables do not fit the memory budget (and for n > 34).
+ *
+ * Element types
+ *   PERM_C128  complex128 entries, row-major, interleaved (re, im) doubles --
+ *              the layout of torch.complex128 / numpy.complex128.  Computed in
+ *              IEEE binary64 (no reduced precision anywhere); the last sum of
+ *              each method is compensated (double-double).
+ *   PERM_U01   0/1 entries stored as int64.  Exact: computed modulo 2^64 or
+ *              2^128, the width chosen per matrix from an upper bound on
+ *              per(A) (min of the products of row sums and of column sums, and
+ *              Bregman's bound), so the result is the exact permanent.
+ *   PERM_I64   small nonnegative integer entries stored as int64.  Exact as
+ *              above (row/column-sum bound).
+ *
+ * Conventions
+ *   - Matrices of one call are concatenated: matrix i starts at element
+ *     offset_i = sum_{j<i} n_j^2 of `mats`.
+ *   - n = 0 is allowed and gives per = 1 (empty product).  1 <= n <= 34 may use
+ *     Store-zechin; Ryser accepts n <= 40 (complex) and n <= 40 (integers).
+ *   - Results: PERM_C128 -> double2 out[count] (re, im).  Integer types ->
+ *     uint64 out[2*count], (low, high) words of a 128-bit unsigned value.
+ *   - `item_status` (optional, device int[count]) receives PERM_OK, or
+ *     PERM_EOVERFLOW when the bound exceeds 2^128 (the result is then per(A)
+ *     mod 2^128), or PERM_EINVAL for an entry that is negative (or not 0/1 for
+ *     PERM_U01).
+ *
+ * Ownership: the caller owns every input and output buffer; the library owns
+ * its workspace (Store-zechin tables, Ryser partial sums, item descriptors),
+ * allocated in perm_plan_create and freed in perm_plan_destroy.  perm_batch
+ * itself never allocates.
+ *
+ * Errors: argument errors are returned synchronously and nothing is launched.
+ * CUDA failures map to PERM_ECUDA.  Per-matrix conditions go to item_status.
+ * No function aborts the process.
+ *
+ * Thread safety: a plan may be used by one host thread at a time; different
+ * plans are independent.
+ */
+#ifndef LIBPERM_H
+#define LIBPERM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum perm_status {
+    PERM_OK = 0,
+    PERM_EINVAL = 1,      /* bad argument (size, pointer, dtype, method) */
+    PERM_ENOMEM = 2,      /* workspace does not fit the budget or the device */
+    PERM_EOVERFLOW = 3,   /* integer bound >= 2^128 (per-item status) */
+    PERM_ECUDA = 4,       /* a CUDA runtime call failed */
+    PERM_EAGAIN = 5,      /* try again: queue full (submit) or not done (poll) */
+    PERM_ETIMEDOUT = 6,   /* a bounded wait gave up */
+    PERM_ESHUTDOWN = 7,   /* the server is shutting down */
+    PERM_ENOTFOUND = 8    /* unknown ticket */
+} perm_status;
+
+typedef enum perm_dtype {
+    PERM_C128 = 1,
+    PERM_U01 = 2,
+    PERM_I64 = 3
+} perm_dtype;
+
+typedef enum perm_method {
+    PERM_METHOD_AUTO = 0,   /* Store-zechin when its tables fit, else Ryser */
+    PERM_METHOD_SZ = 1,     /* Store-zechin only (PERM_ENOMEM if it cannot fit) */
+    PERM_METHOD_RYSER = 2   /* Ryser / Gray code only */
+} perm_method;
+
+/* perm_opts.flags */
+#define PERM_FLAG_PLAIN 1u    /* one kernel launch per matrix (the unbatched baseline) */
+
+typedef struct perm_opts {
+    size_t mem_budget_bytes;  /* workspace cap; 0 = 45% of the free device memory */
+    int max_batch;            /* matrices per perm_batch call; 0 = 65536 */
+    int method;               /* perm_method */
+    unsigned flags;           /* PERM_FLAG_* */
+    int ctas_per_sm;          /* persistent CTAs per SM for batched launches; 0 = tuned */
+    int low_cols;             /* Store-zechin low-column count m (smem chain width); 0 = tuned */
+} perm_opts;
+
+typedef struct perm_plan_s *perm_plan_t;
+typedef struct perm_server_s *perm_server_t;
+
+/* Create a plan for matrices of order <= n_max and element type `dtype` on the
+   current CUDA device.  `opts` may be NULL (all defaults).  Allocates the
+   workspace.  Returns PERM_EINVAL for n_max outside [0, 40] or a bad dtype,
+   PERM_ENOMEM if the workspace does not fit (with PERM_METHOD_SZ forced). */
+perm_status perm_plan_create(int n_max, perm_dtype dtype, const perm_opts *opts,
+                             perm_plan_t *out);
+
+/* Free a plan and its workspace (synchronises the device first). NULL is a no-op. */
+perm_status perm_plan_destroy(perm_plan_t plan);
+
+/* Workspace bytes the plan holds on the device. */
+size_t perm_plan_workspace_bytes(perm_plan_t plan);
+
+/* Permanents of `count` matrices, asynchronously on `stream` (a cudaStream_t;
+   NULL = the legacy default stream).
+     mats        device pointer, concatenated row-major matrices (see above)
+     sizes       HOST int[count], each in [0, n_max]
+     out         device pointer, double2[count] or uint64[2*count]
+     item_status device int[count] or NULL
+   The call returns once the work is enqueued.  Inputs must stay valid and
+   unmodified until the stream reaches that point. */
+perm_status perm_batch(perm_plan_t plan, const void *mats, const int *sizes, int count,
+                       void *out, int *item_status, void *stream);
+
+/* Like perm_batch with HOST buffers: copies the matrices in, computes, copies
+   the results (and statuses, if item_status != NULL) back, and synchronises
+   `stream` before returning.  mats/out/item_status are host pointers. */
+perm_status perm_batch_host(perm_plan_t plan, const void *mats, const int *sizes, int count,
+                            void *out, int *item_status, void *stream);
+
+/* Continuous-batching server (one device, one stream).  Requests of any n and
+   dtype are admitted while their Store-zechin tables fit the memory budget
+   (otherwise they run with Ryser), batched with whatever else is waiting, and
+   completed asynchronously.
+     perm_submit copies the host matrix (n*n elements of `dtype`) and returns a
+       ticket; PERM_EAGAIN if the queue is full.
+     perm_poll returns PERM_EAGAIN until the ticket is done, then writes the 16
+       result bytes (double2, or (low, high) uint64) and the item status.
+     perm_server_destroy stops the server; PERM_ETIMEDOUT if in-flight work
+       does not finish within timeout_ms. */
+perm_status perm_server_create(const perm_opts *opts, void *stream, perm_server_t *out);
+perm_status perm_submit(perm_server_t server, const void *host_mat, int n, perm_dtype dtype,
+                        uint64_t *ticket);
+perm_status perm_poll(perm_server_t server, uint64_t ticket, void *out16, int *item_status);
+perm_status perm_server_destroy(perm_server_t server, int timeout_ms);
+
+/* Short text for a status code (static storage). */
+const char *perm_strerror(perm_status status);
+
+/* Library version as "major.minor.patch" (static storage). */
+const char *perm_version(void);
+
+/* Measurement helper: sustained FP64 fused-multiply-add throughput of the
+   current device in FLOP/s (2 per FMA), timed with CUDA events over `ms_target`
+   milliseconds of independent FMA chains on every SM.  Used as the roofline
+   denominator for the complex kernels.  Returns PERM_ECUDA on failure. */
+perm_status perm_measure_fp64_peak(double ms_target, double *flops_per_s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LIBPERM_H */
