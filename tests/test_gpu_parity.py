@@ -1,0 +1,154 @@
+"""GPU parity: the CUDA Store-zechin and Ryser kernels against the CPU oracle.
+
+Complex results must satisfy |per_gpu - per_oracle| <= 1e-12 * per(|A|);
+integer results must be bit-exact."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1802_02779_gb300 import workloads as wl
+from tests.gpu_helpers import oracle_c, oracle_i, rand01, rand_complex, tol_c
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def lp():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_1802_02779_gb300 import build
+    build.build()
+    from paper_1802_02779_gb300 import libperm
+    libperm.load()
+    return libperm
+
+
+METHODS = ["sz", "ryser"]
+
+
+def meth(lp, name):
+    return {"sz": lp.METHOD_SZ, "ryser": lp.METHOD_RYSER, "auto": lp.METHOD_AUTO}[name]
+
+
+# ---------------------------------------------------------------------------
+# 5-boson workload: all 126 collision-free patterns + 100 0/1 matrices
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("method", METHODS)
+def test_five_boson_complex(lp, method):
+    cm, _ = wl.five_boson()
+    got = lp.permanents(list(cm), "c128", method=meth(lp, method))
+    for g, m in zip(got, cm):
+        assert abs(g - oracle_c(m)) <= tol_c(m)
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_five_boson_01(lp, method):
+    _, im = wl.five_boson()
+    got = lp.permanents(list(im), "u01", method=meth(lp, method))
+    assert got == [oracle_i(m) for m in im]
+
+
+# ---------------------------------------------------------------------------
+# every order, several tiles and ragged chains
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("method", METHODS)
+def test_complex_orders_1_to_18(lp, method):
+    mats = [rand_complex(n, 1000 + n) for n in range(1, 19)]
+    got = lp.permanents(mats, "c128", method=meth(lp, method))
+    for g, m in zip(got, mats):
+        assert abs(g - oracle_c(m)) <= tol_c(m), (m.shape[0], g, oracle_c(m))
+
+
+@pytest.mark.parametrize("method", METHODS)
+@pytest.mark.parametrize("n", [19, 20, 21])
+def test_complex_high_columns(lp, method, n):
+    """n > 13 exercises the high-column chains (t = n - 13 layers)."""
+    mats = [rand_complex(n, 2000 + n + k) for k in range(2)]
+    got = lp.permanents(mats, "c128", method=meth(lp, method))
+    for g, m in zip(got, mats):
+        assert abs(g - oracle_c(m)) <= tol_c(m)
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_01_orders_1_to_22(lp, method):
+    mats = [rand01(n, 3000 + n, p=0.6) for n in range(1, 23)]
+    got = lp.permanents(mats, "u01", method=meth(lp, method))
+    assert got == [oracle_i(m) for m in mats]
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_small_integers(lp, method):
+    g = np.random.default_rng(5)
+    mats = [g.integers(0, 6, size=(n, n)).astype(np.int64) for n in (2, 5, 9, 14, 17)]
+    got = lp.permanents(mats, "i64", method=meth(lp, method))
+    assert got == [oracle_i(m) for m in mats]
+
+
+# ---------------------------------------------------------------------------
+# closed forms and 128-bit integers
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("method", METHODS)
+@pytest.mark.parametrize("n", [20, 21, 23])
+def test_ones_and_derangements_u128(lp, method, n):
+    J = np.ones((n, n), dtype=np.int64)
+    D = J - np.eye(n, dtype=np.int64)
+    got = lp.permanents([J, D], "u01", method=meth(lp, method))
+    d = [1, 0]
+    for k in range(2, n + 1):
+        d.append((k - 1) * (d[-1] + d[-2]))
+    assert got == [math.factorial(n), d[n]]
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_rank_one_complex_closed_form(lp, method):
+    for n in (9, 17, 22):
+        g = np.random.default_rng(40 + n)
+        x = (g.standard_normal(n) + 1j * g.standard_normal(n)) / 2
+        y = (g.standard_normal(n) + 1j * g.standard_normal(n)) / 2
+        want = math.factorial(n) * np.prod(x) * np.prod(y)
+        scale = math.factorial(n) * np.prod(np.abs(x)) * np.prod(np.abs(y))
+        got = lp.permanents([np.outer(x, y)], "c128", method=meth(lp, method))[0]
+        assert abs(got - want) <= 1e-12 * scale, (n, got, want)
+
+
+def test_empty_and_one(lp):
+    got = lp.permanents([np.zeros((0, 0), np.complex128), np.array([[2 - 1j]])], "c128")
+    assert got[0] == 1 and got[1] == 2 - 1j
+    got = lp.permanents([np.zeros((0, 0), np.int64), np.array([[1]])], "u01")
+    assert got == [1, 1]
+
+
+def test_item_status_overflow_and_invalid(lp):
+    big = np.full((4, 4), 1 << 40, dtype=np.int64)          # bound (2^42)^4 = 2^168
+    neg = np.array([[1, -1], [2, 3]], dtype=np.int64)
+    ok = np.array([[1, 2], [3, 4]], dtype=np.int64)
+    res, st = lp.permanents([big, neg, ok], "i64", return_status=True)
+    assert list(st) == [lp.PERM_EOVERFLOW, lp.PERM_EINVAL, lp.PERM_OK]
+    assert res[2] == 10
+    two = np.array([[1, 2], [0, 1]], dtype=np.int64)
+    _, st = lp.permanents([two], "u01", return_status=True)
+    assert list(st) == [lp.PERM_EINVAL]
+
+
+# ---------------------------------------------------------------------------
+# determinism: alone vs batched vs plain launches, bit for bit
+# ---------------------------------------------------------------------------
+def test_alone_vs_mix_bitwise(lp):
+    mats = [rand_complex(n, 7000 + n) for n in (5, 12, 16, 20, 14, 3, 20, 9)]
+    mixed = lp.permanents(mats, "c128")
+    for i, m in enumerate(mats):
+        alone = lp.permanents([m], "c128")[0]
+        assert alone == mixed[i]
+    plain = lp.permanents(mats, "c128", flags=lp.FLAG_PLAIN)
+    assert list(plain) == list(mixed)
+
+
+def test_sz_and_ryser_agree_n24(lp):
+    m = rand_complex(24, 99)
+    a = lp.permanents([m], "c128", method=lp.METHOD_SZ)[0]
+    b = lp.permanents([m], "c128", method=lp.METHOD_RYSER)[0]
+    scale = oracle.per_abs(m)
+    assert abs(a - b) <= 2e-12 * scale
