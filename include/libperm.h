@@ -95,7 +95,7 @@ typedef struct perm_opts {
     int method;               /* perm_method */
     unsigned flags;           /* PERM_FLAG_* */
     int ctas_per_sm;          /* persistent CTAs per SM for batched launches; 0 = tuned */
-    int low_cols;             /* Store-zechin low-column count m, 1..13 (shared-memory chain width); 0 = 13 */
+    int low_cols;             /* Store-zechin low-column count m, 1..13 (shared-memory chain width); 0 = 12 */
 } perm_opts;
 
 typedef struct perm_plan_s *perm_plan_t;

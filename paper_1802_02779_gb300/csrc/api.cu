@@ -30,7 +30,7 @@ struct perm_plan_s {
     unsigned flags = 0;
     int max_batch = 65536;
     int num_sms = 0;
-    int m_low = 13;
+    int m_low = 12;
     size_t budget = 0;
 
     // Store-zechin
@@ -135,7 +135,7 @@ perm_status plan_create_impl(int n_max, perm_dtype dtype, const perm_opts* opts,
     p->method = o.method;
     p->flags = o.flags;
     p->max_batch = o.max_batch ? o.max_batch : 65536;
-    p->m_low = o.low_cols ? o.low_cols : 13;
+    p->m_low = o.low_cols ? o.low_cols : 12;
     cudaError_t e = cudaGetDevice(&p->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
     size_t free_b = 0, total_b = 0;
@@ -149,7 +149,9 @@ perm_status plan_create_impl(int n_max, perm_dtype dtype, const perm_opts* opts,
     if (p->method != PERM_METHOD_RYSER && n_max >= 1) {
         p->sz_batch_nmax = sz_batch_limit(p);
         p->sz_ws_per_cta = sz_matrix_workspace_bytes(dtype, p->sz_batch_nmax, p->m_low);
-        int per_sm = o.ctas_per_sm ? o.ctas_per_sm : 1;
+        if (sz_init_tables() != cudaSuccess) { delete p; return PERM_ECUDA; }
+        int per_sm = o.ctas_per_sm ? o.ctas_per_sm
+                                   : sz_batched_occupancy(dtype, std::max(1, p->sz_batch_nmax), p->m_low);
         p->sz_grid = p->num_sms * per_sm;
         sz_batched = p->sz_ws_per_cta * (size_t)p->sz_grid;
         // largest n whose single-matrix workspace fits the remaining budget

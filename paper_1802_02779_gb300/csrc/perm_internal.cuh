@@ -142,6 +142,8 @@ size_t sz_chain_words(int dtype, int m);                 // 64-bit words per cha
 size_t sz_matrix_workspace_bytes(int dtype, int n, int m);
 int sz_smem_bytes(int dtype, int n, int m);                // dynamic shared memory per CTA
 int sz_threads(int dtype);
+int sz_batched_occupancy(int dtype, int n_max, int m);     // resident CTAs per SM
+cudaError_t sz_init_tables();                              // once per device (idempotent)
 
 // Batched: one CTA per matrix, persistent over `count` items (dynamic order by
 // an atomic counter at *counter, which must be zero at launch).

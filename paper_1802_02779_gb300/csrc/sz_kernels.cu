@@ -16,14 +16,21 @@
 // GPU organisation ("chains").  The columns are split into m low columns
 // 0..m-1 and t = n-m high columns m..n-1.  Every set S is a pair (H, L) of a
 // high part and a low part.  A chain is the 2^m entries (H, L) of one high
-// subset H and all low subsets L; inside a chain entries are ordered by |L|,
-// then by the colex rank of L.  The recurrence splits into
-//     low terms   j in L:  T[(H, L \ j)]  -- the same chain, earlier |L|
-//     high terms  h in H:  T[(H \ h, L)]  -- another chain, same position
-// so one CTA computes one chain in shared memory level by level (|L| =
-// 0..m), gathering low parents from shared memory and streaming high parents,
-// coalesced, from the predecessor chains in global memory.  Chains are
-// processed in layers of |H| = 0..t; layer s needs only layer s-1.
+// subset H and all low subsets L.  The recurrence splits into
+//     low terms   j in L:  T[(H, L \ j)]  -- the same chain, |L| one smaller
+//     high terms  h in H:  T[(H \ h, L)]  -- another chain, same L
+// so one CTA computes one chain in shared memory sub-level by sub-level
+// (|L| = 0..m), gathering low parents from shared memory and streaming high
+// parents, coalesced, from the predecessor chains in global memory.  Chains
+// are processed in layers of |H| = 0..t; layer s needs only layer s-1.
+//
+// Two layouts of a chain:
+//   shared memory  indexed by the bit mask of L (2^m slots), so the low parent
+//                  of (H, L) for column j is simply slot L ^ (1 << j);
+//   global memory  indexed by (|L|, colex rank of L): the entries of one
+//                  sub-level are contiguous, and the predecessor chains use the
+//                  same order, so high-parent reads are coalesced.
+// A table (g_masks) lists the masks in the global order.
 //
 // Complex entries use the three-multiplication form of the complex product
 // (Gauss; error analysis in Higham, "Stability of a method for multiplying
@@ -37,7 +44,7 @@
 // ordinary four-product form.
 //
 // Integer entries are evaluated modulo 2^64 or 2^128 (exact under the bound
-// chosen by decide_width); 0/1 and zero coefficients skip their term.
+// chosen by decide_width); zero coefficients skip their term.
 //
 // Summation order for every entry: low columns ascending, then high columns
 // ascending, i.e. all columns ascending.  The order depends only on (n, m),
@@ -45,14 +52,21 @@
 #include "perm_internal.cuh"
 
 #include <algorithm>
+#include <mutex>
+#include <vector>
 
 namespace perm {
 
 namespace {
 
-constexpr int kBinomDim = 24;            // C(x, y) for x < 24 (t <= 21, m <= 15)
-constexpr int kThreadsC128 = 512;
+constexpr int kBinomDim = 24;            // C(x, y) for x < 24 (t <= 21, m <= 13)
+constexpr int kThreadsC128 = 256;
 constexpr int kThreadsInt = 512;
+constexpr int kMaskTableLen = (2 << kMaxLow) - 2;   // sum_{m=1..13} 2^m
+
+// masks of all subsets of {0..m-1}, ordered by (popcount, value); the table
+// of chain width m starts at index 2^m - 2.
+__device__ unsigned short g_masks[kMaskTableLen];
 
 __host__ __device__ inline unsigned long long binom_calc(int n, int k) {
     if (k < 0 || k > n) return 0;
@@ -62,60 +76,49 @@ __host__ __device__ inline unsigned long long binom_calc(int n, int k) {
     return r;
 }
 
+enum ElemKind : int { kC128 = 0, kU64 = 1, kU128 = 2 };
+
+__host__ __device__ inline int chain_bytes_smem(int kind, int m) {
+    return (kind == kC128 ? 24 : (kind == kU64 ? 8 : 16)) << m;
+}
+__host__ __device__ inline int coef_bytes(int kind, int n) {
+    return (kind == kC128 ? 24 : 8) * n * n;
+}
+
 // Shared-memory layout, 16-byte aligned pieces.
 struct SmemLayout {
     int binom_off;      // unsigned[kBinomDim][kBinomDim + 1]
     int hinfo_off;      // int[2 * kBinomDim]: predecessor slot, column
-    int coef_off;       // coefficient planes (n x n each)
-    int chain_off;      // chain planes (2^m each)
+    int coef_off;       // C128: double2 xy[n*n] then double s[n*n]; ints: u64[n*n]
+    int chain_off;      // C128: double2 uv[2^m] then double w[2^m]; u64[2^m]; ulonglong2[2^m]
     int total;
 };
 
 __host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
 
-__host__ __device__ inline SmemLayout smem_layout(int coef_planes, int chain_planes, int n, int m) {
+__host__ __device__ inline SmemLayout smem_layout(int kind, int n, int m) {
     SmemLayout s;
     s.binom_off = 0;
     s.hinfo_off = align16(s.binom_off + kBinomDim * (kBinomDim + 1) * 4);
     s.coef_off = align16(s.hinfo_off + 2 * kBinomDim * 4);
-    s.chain_off = align16(s.coef_off + coef_planes * n * n * 8);
-    s.total = align16(s.chain_off + chain_planes * (1 << m) * 8);
+    s.chain_off = align16(s.coef_off + coef_bytes(kind, n));
+    s.total = align16(s.chain_off + chain_bytes_smem(kind, m));
     return s;
 }
-
-// Element kinds ------------------------------------------------------------
-
-struct KindC128 { static constexpr int kPlanes = 3; };   // u, v, w (coefficients x, y, s)
-struct KindU64 { static constexpr int kPlanes = 1; };
-struct KindU128 { static constexpr int kPlanes = 2; };   // low, high words
 
 struct u128 { unsigned long long lo, hi; };
 
 __device__ __forceinline__ u128 u128_mac(u128 acc, unsigned long long c, unsigned long long plo,
                                          unsigned long long phi) {
     // acc + c * (phi:plo)  mod 2^128
-    unsigned long long lo = c * plo;
-    unsigned long long hi = __umul64hi(c, plo) + c * phi;
-    unsigned long long nlo = acc.lo + lo;
-    unsigned long long carry = nlo < lo ? 1ull : 0ull;
-    return {nlo, acc.hi + hi + carry};
+    const unsigned long long lo = c * plo;
+    const unsigned long long hi = __umul64hi(c, plo) + c * phi;
+    const unsigned long long nlo = acc.lo + lo;
+    return {nlo, acc.hi + hi + (nlo < lo ? 1ull : 0ull)};
 }
-
-// Colex unranking of an l-subset of {0..m-1}: returns the bit mask and
-// sum_p C(s_p, p) (the "shifted" rank used for parent indices).
-__device__ __forceinline__ unsigned unrank_low(unsigned r, int l, int m, const unsigned* bn,
-                                               unsigned& shifted) {
-    unsigned mask = 0, tb = 0;
-    int c = m - 1;
-    for (int p = l - 1; p >= 0; p--) {
-        while (bn[c * (kBinomDim + 1) + p + 1] > r) c--;
-        mask |= 1u << c;
-        r -= bn[c * (kBinomDim + 1) + p + 1];
-        tb += bn[c * (kBinomDim + 1) + p];
-        c--;
-    }
-    shifted = tb;
-    return mask;
+__device__ __forceinline__ u128 u128_add2(u128 acc, unsigned long long plo, unsigned long long phi) {
+    const unsigned long long nlo = acc.lo + plo;
+    return {nlo, acc.hi + phi + (nlo < plo ? 1ull : 0ull)};
 }
 
 // Context of one matrix inside one CTA.
@@ -124,18 +127,8 @@ struct MatCtx {
     unsigned chain_len;          // 2^m
     const unsigned* bn;          // smem binomials
     const int* hinfo;            // smem: [0..s) predecessor slots, [kBinomDim..) columns
+    const unsigned short* masks; // mask list of this m (global)
 };
-
-// ---------------------------------------------------------------------------
-// One chain (high subset H with |H| = s, slot = colex rank of H among the
-// s-subsets of the t high columns).  Writes the chain to `gdst` (global, may
-// be null) and, if it is the last chain, the permanent to the output.
-// `gprev` is the previous layer's region (chains of |H| = s-1).
-// ---------------------------------------------------------------------------
-template <class Kind>
-__device__ void process_chain(const MatCtx& mc, unsigned Hmask, int s, unsigned long long* chain_smem,
-                              const unsigned long long* gprev, unsigned long long* gdst,
-                              const void* coef_smem, bool last, void* out, int out_index);
 
 // Predecessor info for chain H: for the p-th high element h_p (ascending),
 // the slot of H \ h_p among the (s-1)-subsets and the matrix column m + h_p.
@@ -158,257 +151,240 @@ __device__ __forceinline__ void chain_setup(const MatCtx& mc, unsigned Hmask, in
     }
 }
 
-// ---- complex128 ------------------------------------------------------------
-template <>
-__device__ void process_chain<KindC128>(const MatCtx& mc, unsigned Hmask, int s,
-                                        unsigned long long* chain_smem_u,
-                                        const unsigned long long* gprev_u,
-                                        unsigned long long* gdst_u, const void* coef_smem,
-                                        bool last, void* out, int out_index) {
+// ---------------------------------------------------------------------------
+// complex128 chain.  gprev: previous layer region (chains of 3*CL doubles:
+// uv plane then w plane); gdst: this chain's slot or null.
+// ---------------------------------------------------------------------------
+__device__ void chain_c128(const MatCtx& mc, int s, unsigned char* chain_smem, const double* gprev,
+                           double* gdst, const unsigned char* coef_smem, bool last, double2* out,
+                           int out_index) {
     const int n = mc.n, m = mc.m;
     const unsigned CL = mc.chain_len;
-    double* ch = reinterpret_cast<double*>(chain_smem_u);
-    const double* gprev = reinterpret_cast<const double*>(gprev_u);
-    double* gdst = reinterpret_cast<double*>(gdst_u);
-    const double* cx = reinterpret_cast<const double*>(coef_smem);
-    const double* cy = cx + n * n;
-    const double* cs = cy + n * n;
+    double2* suv = reinterpret_cast<double2*>(chain_smem);
+    double* sw = reinterpret_cast<double*>(chain_smem + 16 * CL);
+    const double2* cxy = reinterpret_cast<const double2*>(coef_smem);
+    const double* cs = reinterpret_cast<const double*>(coef_smem + 16 * n * n);
     const unsigned* bn = mc.bn;
     const int* hslot = mc.hinfo;
     const int* hcol = mc.hinfo + kBinomDim;
+    const unsigned short* masks = mc.masks;
 
-    unsigned off_prev = 0, off = 0;
+    unsigned off = 0;
     for (int l = 0; l <= m; l++) {
         const unsigned cnt = bn[m * (kBinomDim + 1) + l];
         const int k = s + l;
-        const int row = k - 1;
+        const int row = k >= 1 ? k - 1 : 0;
+        const double2* rxy = cxy + row * n;
+        const double* rs = cs + row * n;
         for (unsigned r = threadIdx.x; r < cnt; r += blockDim.x) {
             const unsigned idx = off + r;
+            const unsigned mask = masks[idx];
             double u, v, w;
             if (k == 0) {
                 u = 1.0; v = 0.0; w = 1.0;
             } else if (k == 1) {
-                // the single column of S
-                int col;
-                if (l == 1) { unsigned tb; col = __ffs(unrank_low(r, 1, m, bn, tb)) - 1; }
-                else col = hcol[0];
-                u = cx[col]; v = cy[col]; w = cs[col];
+                const int col = (l == 1) ? __ffs(mask) - 1 : hcol[0];
+                u = cxy[col].x; v = cxy[col].y; w = cs[col];
             } else if (k == n) {
                 // the permanent: double-double, four-product complex form
                 dd2 re = {0.0, 0.0}, im = {0.0, 0.0};
-                unsigned tb;
-                unsigned mask = unrank_low(r, l, m, bn, tb);
-                unsigned A = 0, Bp = 0;
-                int p = 0;
-                while (mask) {
-                    const int j = __ffs(mask) - 1;
-                    mask &= mask - 1;
-                    const unsigned pidx = off_prev + A + (tb - Bp - bn[j * (kBinomDim + 1) + p]);
-                    A += bn[j * (kBinomDim + 1) + p + 1];
-                    Bp += bn[j * (kBinomDim + 1) + p];
-                    p++;
-                    const double x = cx[row * n + j], y = cy[row * n + j];
-                    const double pu = ch[pidx], pv = ch[CL + pidx];
-                    re = dd_add_prod(re, x, pu);
-                    re = dd_add_prod(re, -y, pv);
-                    im = dd_add_prod(im, x, pv);
-                    im = dd_add_prod(im, y, pu);
+                unsigned mm = mask;
+                while (mm) {
+                    const int j = __ffs(mm) - 1;
+                    mm &= mm - 1;
+                    const double2 p = suv[mask ^ (1u << j)];
+                    const double2 c = rxy[j];
+                    re = dd_add_prod(re, c.x, p.x);
+                    re = dd_add_prod(re, -c.y, p.y);
+                    im = dd_add_prod(im, c.x, p.y);
+                    im = dd_add_prod(im, c.y, p.x);
                 }
                 for (int q = 0; q < s; q++) {
-                    const double* pc = gprev + (size_t)hslot[q] * 3 * CL;
-                    const int col = hcol[q];
-                    const double x = cx[row * n + col], y = cy[row * n + col];
-                    const double pu = pc[idx], pv = pc[CL + idx];
-                    re = dd_add_prod(re, x, pu);
-                    re = dd_add_prod(re, -y, pv);
-                    im = dd_add_prod(im, x, pv);
-                    im = dd_add_prod(im, y, pu);
+                    const double2 p = reinterpret_cast<const double2*>(gprev + (size_t)hslot[q] * 3 * CL)[idx];
+                    const double2 c = rxy[hcol[q]];
+                    re = dd_add_prod(re, c.x, p.x);
+                    re = dd_add_prod(re, -c.y, p.y);
+                    im = dd_add_prod(im, c.x, p.y);
+                    im = dd_add_prod(im, c.y, p.x);
                 }
                 u = dd_round(re); v = dd_round(im); w = __dadd_rn(u, v);
             } else {
+                // prefetch up to four high parents before the shared-memory terms
+                double2 huv[4];
+                double hw[4];
+#pragma unroll
+                for (int z = 0; z < 4; z++) {
+                    if (z < s) {
+                        const double* pc = gprev + (size_t)hslot[z] * 3 * CL;
+                        huv[z] = __ldg(reinterpret_cast<const double2*>(pc) + idx);
+                        hw[z] = __ldg(pc + 2 * CL + idx);
+                    }
+                }
                 double P1 = 0.0, P2 = 0.0, P3 = 0.0;
-                unsigned tb;
-                unsigned mask = unrank_low(r, l, m, bn, tb);
-                unsigned A = 0, Bp = 0;
-                int p = 0;
-                const double* rx = cx + row * n;
-                const double* ry = cy + row * n;
-                const double* rs = cs + row * n;
-                while (mask) {
-                    const int j = __ffs(mask) - 1;
-                    mask &= mask - 1;
-                    const unsigned pidx = off_prev + A + (tb - Bp - bn[j * (kBinomDim + 1) + p]);
-                    A += bn[j * (kBinomDim + 1) + p + 1];
-                    Bp += bn[j * (kBinomDim + 1) + p];
-                    p++;
-                    P1 = __fma_rn(rx[j], ch[pidx], P1);
-                    P2 = __fma_rn(ry[j], ch[CL + pidx], P2);
-                    P3 = __fma_rn(rs[j], ch[2 * CL + pidx], P3);
+                unsigned mm = mask;
+                while (mm) {
+                    const int j = __ffs(mm) - 1;
+                    mm &= mm - 1;
+                    const unsigned pm = mask ^ (1u << j);
+                    const double2 p = suv[pm];
+                    const double pw = sw[pm];
+                    const double2 c = rxy[j];
+                    P1 = __fma_rn(c.x, p.x, P1);
+                    P2 = __fma_rn(c.y, p.y, P2);
+                    P3 = __fma_rn(rs[j], pw, P3);
                 }
-                // high terms: predecessor chains, same position; prefetch in groups of 4
-                int q = 0;
-                for (; q + 4 <= s; q += 4) {
-                    double gu[4], gv[4], gw[4];
+#pragma unroll
+                for (int z = 0; z < 4; z++) {
+                    if (z < s) {
+                        const int col = hcol[z];
+                        const double2 c = rxy[col];
+                        P1 = __fma_rn(c.x, huv[z].x, P1);
+                        P2 = __fma_rn(c.y, huv[z].y, P2);
+                        P3 = __fma_rn(rs[col], hw[z], P3);
+                    }
+                }
+                for (int q = 4; q < s; q += 4) {
 #pragma unroll
                     for (int z = 0; z < 4; z++) {
-                        const double* pc = gprev + (size_t)hslot[q + z] * 3 * CL + idx;
-                        gu[z] = __ldg(pc);
-                        gv[z] = __ldg(pc + CL);
-                        gw[z] = __ldg(pc + 2 * CL);
+                        if (q + z < s) {
+                            const double* pc = gprev + (size_t)hslot[q + z] * 3 * CL;
+                            huv[z] = __ldg(reinterpret_cast<const double2*>(pc) + idx);
+                            hw[z] = __ldg(pc + 2 * CL + idx);
+                        }
                     }
 #pragma unroll
                     for (int z = 0; z < 4; z++) {
-                        const int col = hcol[q + z];
-                        P1 = __fma_rn(rx[col], gu[z], P1);
-                        P2 = __fma_rn(ry[col], gv[z], P2);
-                        P3 = __fma_rn(rs[col], gw[z], P3);
+                        if (q + z < s) {
+                            const int col = hcol[q + z];
+                            const double2 c = rxy[col];
+                            P1 = __fma_rn(c.x, huv[z].x, P1);
+                            P2 = __fma_rn(c.y, huv[z].y, P2);
+                            P3 = __fma_rn(rs[col], hw[z], P3);
+                        }
                     }
-                }
-                for (; q < s; q++) {
-                    const double* pc = gprev + (size_t)hslot[q] * 3 * CL + idx;
-                    const int col = hcol[q];
-                    P1 = __fma_rn(rx[col], __ldg(pc), P1);
-                    P2 = __fma_rn(ry[col], __ldg(pc + CL), P2);
-                    P3 = __fma_rn(rs[col], __ldg(pc + 2 * CL), P3);
                 }
                 u = __dsub_rn(P1, P2);
                 v = __dsub_rn(__dsub_rn(P3, P1), P2);
                 w = __dadd_rn(u, v);
             }
-            ch[idx] = u; ch[CL + idx] = v; ch[2 * CL + idx] = w;
-            if (gdst) { gdst[idx] = u; gdst[CL + idx] = v; gdst[2 * CL + idx] = w; }
-            if (last && l == m) {
-                reinterpret_cast<double2*>(out)[out_index] = make_double2(u, v);
+            suv[mask] = make_double2(u, v);
+            sw[mask] = w;
+            if (gdst) {
+                reinterpret_cast<double2*>(gdst)[idx] = make_double2(u, v);
+                gdst[2 * CL + idx] = w;
             }
+            if (last && l == m) out[out_index] = make_double2(u, v);
         }
-        off_prev = off;
         off += cnt;
         __syncthreads();
     }
 }
 
-// ---- integers modulo 2^64 --------------------------------------------------
-template <>
-__device__ void process_chain<KindU64>(const MatCtx& mc, unsigned Hmask, int s,
-                                       unsigned long long* ch, const unsigned long long* gprev,
-                                       unsigned long long* gdst, const void* coef_smem, bool last,
-                                       void* out, int out_index) {
+// ---------------------------------------------------------------------------
+// integer chain modulo 2^64 (W128 = false) or 2^128 (W128 = true).
+// ZO: coefficients are 0/1 (add instead of multiply-add).
+// Global chain: CL words (u64) or CL ulonglong2 (u128).
+// ---------------------------------------------------------------------------
+template <bool W128, bool ZO>
+__device__ void chain_int(const MatCtx& mc, int s, unsigned char* chain_smem,
+                          const unsigned long long* gprev, unsigned long long* gdst,
+                          const unsigned long long* coef, bool last, unsigned long long* out,
+                          int out_index) {
     const int n = mc.n, m = mc.m;
     const unsigned CL = mc.chain_len;
-    const unsigned long long* co = reinterpret_cast<const unsigned long long*>(coef_smem);
     const unsigned* bn = mc.bn;
     const int* hslot = mc.hinfo;
     const int* hcol = mc.hinfo + kBinomDim;
-    unsigned off_prev = 0, off = 0;
-    for (int l = 0; l <= m; l++) {
-        const unsigned cnt = bn[m * (kBinomDim + 1) + l];
-        const int k = s + l;
-        const unsigned long long* rc = co + (k >= 1 ? (k - 1) * n : 0);
-        for (unsigned r = threadIdx.x; r < cnt; r += blockDim.x) {
-            const unsigned idx = off + r;
-            unsigned long long val;
-            if (k == 0) {
-                val = 1ull;
-            } else if (k == 1) {
-                int col;
-                if (l == 1) { unsigned tb; col = __ffs(unrank_low(r, 1, m, bn, tb)) - 1; }
-                else col = hcol[0];
-                val = co[col];
-            } else {
-                val = 0ull;
-                unsigned tb;
-                unsigned mask = unrank_low(r, l, m, bn, tb);
-                unsigned A = 0, Bp = 0;
-                int p = 0;
-                while (mask) {
-                    const int j = __ffs(mask) - 1;
-                    mask &= mask - 1;
-                    const unsigned pidx = off_prev + A + (tb - Bp - bn[j * (kBinomDim + 1) + p]);
-                    A += bn[j * (kBinomDim + 1) + p + 1];
-                    Bp += bn[j * (kBinomDim + 1) + p];
-                    p++;
-                    const unsigned long long c = rc[j];
-                    if (c) val += c * ch[pidx];
-                }
-                for (int q = 0; q < s; q++) {
-                    const unsigned long long c = rc[hcol[q]];
-                    if (c) val += c * __ldg(gprev + (size_t)hslot[q] * CL + idx);
-                }
-            }
-            ch[idx] = val;
-            if (gdst) gdst[idx] = val;
-            if (last && l == m) {
-                unsigned long long* o = reinterpret_cast<unsigned long long*>(out);
-                o[2 * out_index] = val;
-                o[2 * out_index + 1] = 0ull;
-            }
-        }
-        off_prev = off;
-        off += cnt;
-        __syncthreads();
-    }
-}
+    const unsigned short* masks = mc.masks;
+    constexpr int kW = W128 ? 2 : 1;     // words per entry
+    unsigned long long* sv = reinterpret_cast<unsigned long long*>(chain_smem);
+    ulonglong2* sv2 = reinterpret_cast<ulonglong2*>(chain_smem);
 
-// ---- integers modulo 2^128 -------------------------------------------------
-template <>
-__device__ void process_chain<KindU128>(const MatCtx& mc, unsigned Hmask, int s,
-                                        unsigned long long* ch, const unsigned long long* gprev,
-                                        unsigned long long* gdst, const void* coef_smem, bool last,
-                                        void* out, int out_index) {
-    const int n = mc.n, m = mc.m;
-    const unsigned CL = mc.chain_len;
-    const unsigned long long* co = reinterpret_cast<const unsigned long long*>(coef_smem);
-    const unsigned* bn = mc.bn;
-    const int* hslot = mc.hinfo;
-    const int* hcol = mc.hinfo + kBinomDim;
-    unsigned off_prev = 0, off = 0;
+    unsigned off = 0;
     for (int l = 0; l <= m; l++) {
         const unsigned cnt = bn[m * (kBinomDim + 1) + l];
         const int k = s + l;
-        const unsigned long long* rc = co + (k >= 1 ? (k - 1) * n : 0);
+        const unsigned long long* rc = coef + (k >= 1 ? (k - 1) * n : 0);
         for (unsigned r = threadIdx.x; r < cnt; r += blockDim.x) {
             const unsigned idx = off + r;
-            u128 val;
+            const unsigned mask = masks[idx];
+            u128 val = {0ull, 0ull};
             if (k == 0) {
-                val = {1ull, 0ull};
+                val.lo = 1ull;
             } else if (k == 1) {
-                int col;
-                if (l == 1) { unsigned tb; col = __ffs(unrank_low(r, 1, m, bn, tb)) - 1; }
-                else col = hcol[0];
-                val = {co[col], 0ull};
+                const int col = (l == 1) ? __ffs(mask) - 1 : hcol[0];
+                val.lo = coef[col];
             } else {
-                val = {0ull, 0ull};
-                unsigned tb;
-                unsigned mask = unrank_low(r, l, m, bn, tb);
-                unsigned A = 0, Bp = 0;
-                int p = 0;
-                while (mask) {
-                    const int j = __ffs(mask) - 1;
-                    mask &= mask - 1;
-                    const unsigned pidx = off_prev + A + (tb - Bp - bn[j * (kBinomDim + 1) + p]);
-                    A += bn[j * (kBinomDim + 1) + p + 1];
-                    Bp += bn[j * (kBinomDim + 1) + p];
-                    p++;
-                    const unsigned long long c = rc[j];
-                    if (c) val = u128_mac(val, c, ch[pidx], ch[CL + pidx]);
+                // high parents whose coefficient is nonzero (a uniform test), prefetched
+                unsigned long long hlo[4], hhi[4];
+#pragma unroll
+                for (int z = 0; z < 4; z++) {
+                    hlo[z] = 0ull; hhi[z] = 0ull;
+                    if (z < s && rc[hcol[z]] != 0ull) {
+                        const unsigned long long* pc = gprev + (size_t)hslot[z] * kW * CL;
+                        if (W128) {
+                            const ulonglong2 p = __ldg(reinterpret_cast<const ulonglong2*>(pc) + idx);
+                            hlo[z] = p.x; hhi[z] = p.y;
+                        } else {
+                            hlo[z] = __ldg(pc + idx);
+                        }
+                    }
                 }
-                for (int q = 0; q < s; q++) {
-                    const unsigned long long c = rc[hcol[q]];
+                unsigned mm = mask;
+                while (mm) {
+                    const int j = __ffs(mm) - 1;
+                    mm &= mm - 1;
+                    const unsigned long long c = rc[j];
                     if (c) {
-                        const unsigned long long* pc = gprev + (size_t)hslot[q] * 2 * CL + idx;
-                        val = u128_mac(val, c, __ldg(pc), __ldg(pc + CL));
+                        const unsigned pm = mask ^ (1u << j);
+                        if (W128) {
+                            const ulonglong2 p = sv2[pm];
+                            val = ZO ? u128_add2(val, p.x, p.y) : u128_mac(val, c, p.x, p.y);
+                        } else {
+                            val.lo += ZO ? sv[pm] : c * sv[pm];
+                        }
+                    }
+                }
+                for (int q = 0; q < s; q += 4) {
+                    if (q > 0) {
+#pragma unroll
+                        for (int z = 0; z < 4; z++) {
+                            hlo[z] = 0ull; hhi[z] = 0ull;
+                            if (q + z < s && rc[hcol[q + z]] != 0ull) {
+                                const unsigned long long* pc = gprev + (size_t)hslot[q + z] * kW * CL;
+                                if (W128) {
+                                    const ulonglong2 p = __ldg(reinterpret_cast<const ulonglong2*>(pc) + idx);
+                                    hlo[z] = p.x; hhi[z] = p.y;
+                                } else {
+                                    hlo[z] = __ldg(pc + idx);
+                                }
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int z = 0; z < 4; z++) {
+                        if (q + z < s) {
+                            const unsigned long long c = rc[hcol[q + z]];
+                            if (c) {
+                                if (W128) val = ZO ? u128_add2(val, hlo[z], hhi[z]) : u128_mac(val, c, hlo[z], hhi[z]);
+                                else val.lo += ZO ? hlo[z] : c * hlo[z];
+                            }
+                        }
                     }
                 }
             }
-            ch[idx] = val.lo; ch[CL + idx] = val.hi;
-            if (gdst) { gdst[idx] = val.lo; gdst[CL + idx] = val.hi; }
+            if (W128) {
+                sv2[mask] = make_ulonglong2(val.lo, val.hi);
+                if (gdst) reinterpret_cast<ulonglong2*>(gdst)[idx] = make_ulonglong2(val.lo, val.hi);
+            } else {
+                sv[mask] = val.lo;
+                if (gdst) gdst[idx] = val.lo;
+            }
             if (last && l == m) {
-                unsigned long long* o = reinterpret_cast<unsigned long long*>(out);
-                o[2 * out_index] = val.lo;
-                o[2 * out_index + 1] = val.hi;
+                out[2 * out_index] = val.lo;
+                out[2 * out_index + 1] = W128 ? val.hi : 0ull;
             }
         }
-        off_prev = off;
         off += cnt;
         __syncthreads();
     }
@@ -434,51 +410,79 @@ __device__ inline void fill_binom(unsigned* bn) {
     }
 }
 
-// Load the coefficient planes of one matrix into shared memory.
-__device__ inline void load_coef_c128(const double2* a, int n, double* coef) {
+// Load the coefficients of one matrix into shared memory.
+__device__ inline void load_coef_c128(const double2* a, int n, unsigned char* coef) {
+    double2* xy = reinterpret_cast<double2*>(coef);
+    double* sm = reinterpret_cast<double*>(coef + 16 * n * n);
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
         const double2 z = a[e];
-        coef[e] = z.x;
-        coef[n * n + e] = z.y;
-        coef[2 * n * n + e] = __dadd_rn(z.x, z.y);
+        xy[e] = z;
+        sm[e] = __dadd_rn(z.x, z.y);
     }
 }
 __device__ inline void load_coef_int(const long long* a, int n, unsigned long long* coef) {
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) coef[e] = (unsigned long long)a[e];
 }
 
-// All chains of one matrix, inside one CTA (batched mode).
-template <class Kind>
-__device__ void run_matrix_cta(MatCtx& mc, unsigned long long* chain_smem, unsigned long long* ws,
-                               const void* coef, void* out, int out_index, int* hinfo_smem) {
-    const size_t CW = (size_t)Kind::kPlanes * mc.chain_len;
+__device__ inline void init_ctx(MatCtx& mc, int n, int m_param, const unsigned char* smem,
+                                const SmemLayout& L) {
+    mc.n = n;
+    mc.m = sz_low_for(n, m_param);
+    mc.t = n - mc.m;
+    mc.chain_len = 1u << mc.m;
+    mc.bn = reinterpret_cast<const unsigned*>(smem + L.binom_off);
+    mc.hinfo = reinterpret_cast<const int*>(smem + L.hinfo_off);
+    mc.masks = g_masks + ((1 << mc.m) - 2);
+}
+
+// Global-memory words of one chain.
+__host__ __device__ inline size_t chain_words(int kind, int m) {
+    return (size_t)(kind == kC128 ? 3 : (kind == kU64 ? 1 : 2)) << m;
+}
+
+// One chain of a matrix, any element kind.
+template <int KIND, bool ZO>
+__device__ __forceinline__ void run_chain(const MatCtx& mc, int s, unsigned char* smem_chain,
+                                          const unsigned long long* src, unsigned long long* dst,
+                                          const unsigned char* coef, bool last, void* out,
+                                          int out_index) {
+    if (KIND == kC128)
+        chain_c128(mc, s, smem_chain, reinterpret_cast<const double*>(src),
+                   reinterpret_cast<double*>(dst), coef, last, reinterpret_cast<double2*>(out),
+                   out_index);
+    else
+        chain_int<KIND == kU128, ZO>(mc, s, smem_chain, src, dst,
+                                     reinterpret_cast<const unsigned long long*>(coef), last,
+                                     reinterpret_cast<unsigned long long*>(out), out_index);
+}
+
+// All chains of one matrix, inside one CTA (batched mode).  ws: this CTA's
+// workspace, two layer regions of C(t, t/2) chains each.
+template <int KIND, bool ZO>
+__device__ void run_matrix_cta(const MatCtx& mc, unsigned char* smem_chain, unsigned long long* ws,
+                               const unsigned char* coef, void* out, int out_index, int* hinfo) {
+    const size_t CW = chain_words(KIND, mc.m);
     const size_t layer_words = (size_t)binom_calc(mc.t, mc.t / 2) * CW;
     for (int s = 0; s <= mc.t; s++) {
         const unsigned nslots = (unsigned)binom_calc(mc.t, s);
         unsigned long long* dst_region = ws + (size_t)(s & 1) * layer_words;
         const unsigned long long* src_region = ws + (size_t)((s + 1) & 1) * layer_words;
+        const bool last = (s == mc.t);
         for (unsigned slot = 0; slot < nslots; slot++) {
-            const unsigned H = unrank_high(slot, s, mc.t, mc.bn);
-            chain_setup(mc, H, hinfo_smem);
+            chain_setup(mc, unrank_high(slot, s, mc.t, mc.bn), hinfo);
             __syncthreads();
-            const bool last = (s == mc.t);
-            process_chain<Kind>(mc, H, s, chain_smem, src_region,
+            run_chain<KIND, ZO>(mc, s, smem_chain, src_region,
                                 last ? nullptr : dst_region + (size_t)slot * CW, coef, last, out,
                                 out_index);
-            // process_chain ends with __syncthreads()
+            // every chain ends with __syncthreads()
         }
     }
-}
-
-template <class Kind>
-__device__ void write_status(int* item_status, int idx, int st) {
-    if (item_status && threadIdx.x == 0) item_status[idx] = st;
 }
 
 // ---------------------------------------------------------------------------
 // Batched kernels: one CTA per matrix, persistent over the item list.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreadsC128)
+__global__ void __launch_bounds__(kThreadsC128, 2)
 sz_batched_c128(const double2* __restrict__ mats, const ItemDesc* __restrict__ items, int count,
                 int m_param, double2* out, int* item_status, unsigned long long* workspace,
                 size_t ws_words_per_cta, unsigned* counter) {
@@ -493,27 +497,25 @@ sz_batched_c128(const double2* __restrict__ mats, const ItemDesc* __restrict__ i
         if (it >= count) break;
         const ItemDesc d = items[it];
         const int n = d.n;
+        const SmemLayout L = smem_layout(kC128, n, sz_low_for(n, m_param));
         MatCtx mc;
-        mc.n = n;
-        mc.m = sz_low_for(n, m_param);
-        mc.t = n - mc.m;
-        mc.chain_len = 1u << mc.m;
-        const SmemLayout L = smem_layout(3, 3, n, mc.m);
-        mc.bn = reinterpret_cast<const unsigned*>(smem + L.binom_off);
-        mc.hinfo = reinterpret_cast<const int*>(smem + L.hinfo_off);
-        double* coef = reinterpret_cast<double*>(smem + L.coef_off);
-        load_coef_c128(mats + d.offset, n, coef);
+        init_ctx(mc, n, m_param, smem, L);
+        load_coef_c128(mats + d.offset, n, smem + L.coef_off);
         __syncthreads();
-        run_matrix_cta<KindC128>(mc, reinterpret_cast<unsigned long long*>(smem + L.chain_off),
-                                 workspace + (size_t)blockIdx.x * ws_words_per_cta, coef, out,
-                                 d.out_index, reinterpret_cast<int*>(smem + L.hinfo_off));
-        write_status<KindC128>(item_status, d.out_index, PERM_OK);
+        run_matrix_cta<kC128, false>(mc, smem + L.chain_off,
+                                     workspace + (size_t)blockIdx.x * ws_words_per_cta,
+                                     smem + L.coef_off, out, d.out_index,
+                                     reinterpret_cast<int*>(smem + L.hinfo_off));
+        if (item_status && threadIdx.x == 0) item_status[d.out_index] = PERM_OK;
     }
 }
 
+// W64ONLY: the host guarantees every item fits 64 bits (0/1 input, n <= 20),
+// so the chain needs only one word per entry.
+template <bool ZO, bool W64ONLY>
 __global__ void __launch_bounds__(kThreadsInt)
 sz_batched_int(const long long* __restrict__ mats, const ItemDesc* __restrict__ items, int count,
-               int m_param, int zero_one, unsigned long long* out, int* item_status,
+               int m_param, unsigned long long* out, int* item_status,
                unsigned long long* workspace, size_t ws_words_per_cta, unsigned* counter) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_item;
@@ -527,104 +529,83 @@ sz_batched_int(const long long* __restrict__ mats, const ItemDesc* __restrict__ 
         if (it >= count) break;
         const ItemDesc d = items[it];
         const int n = d.n;
-        if (threadIdx.x == 0) s_width = decide_width(mats + d.offset, n, zero_one != 0);
+        if (threadIdx.x == 0) s_width = decide_width(mats + d.offset, n, ZO);
+        const SmemLayout L = smem_layout(W64ONLY ? kU64 : kU128, n, sz_low_for(n, m_param));
         MatCtx mc;
-        mc.n = n;
-        mc.m = sz_low_for(n, m_param);
-        mc.t = n - mc.m;
-        mc.chain_len = 1u << mc.m;
-        const SmemLayout L = smem_layout(1, 2, n, mc.m);
-        mc.bn = reinterpret_cast<const unsigned*>(smem + L.binom_off);
-        mc.hinfo = reinterpret_cast<const int*>(smem + L.hinfo_off);
+        init_ctx(mc, n, m_param, smem, L);
         unsigned long long* coef = reinterpret_cast<unsigned long long*>(smem + L.coef_off);
         load_coef_int(mats + d.offset, n, coef);
         __syncthreads();
         const int w = s_width;
         unsigned long long* ws = workspace + (size_t)blockIdx.x * ws_words_per_cta;
-        unsigned long long* chain = reinterpret_cast<unsigned long long*>(smem + L.chain_off);
         int* hinfo = reinterpret_cast<int*>(smem + L.hinfo_off);
-        if (w == kWidth64)
-            run_matrix_cta<KindU64>(mc, chain, ws, coef, out, d.out_index, hinfo);
+        if (W64ONLY || w == kWidth64)
+            run_matrix_cta<kU64, ZO>(mc, smem + L.chain_off, ws, smem + L.coef_off, out, d.out_index, hinfo);
         else
-            run_matrix_cta<KindU128>(mc, chain, ws, coef, out, d.out_index, hinfo);
-        write_status<KindU64>(item_status, d.out_index, width_status(w));
+            run_matrix_cta<kU128, ZO>(mc, smem + L.chain_off, ws, smem + L.coef_off, out, d.out_index, hinfo);
+        if (item_status && threadIdx.x == 0) item_status[d.out_index] = width_status(w);
     }
 }
 
 // ---------------------------------------------------------------------------
 // Single-matrix kernels: one launch per layer s; CTAs stride over the slots.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreadsC128)
-sz_layer_c128(const double2* __restrict__ a, int n, int m, int s, double2* out, int out_index,
+__global__ void __launch_bounds__(kThreadsC128, 2)
+sz_layer_c128(const double2* __restrict__ a, int n, int m_param, int s, double2* out, int out_index,
               int* item_status, unsigned long long* workspace) {
     extern __shared__ __align__(16) unsigned char smem[];
     fill_binom(reinterpret_cast<unsigned*>(smem));
+    const SmemLayout L = smem_layout(kC128, n, sz_low_for(n, m_param));
     MatCtx mc;
-    mc.n = n;
-    mc.m = m;
-    mc.t = n - m;
-    mc.chain_len = 1u << m;
-    const SmemLayout L = smem_layout(3, 3, n, m);
-    mc.bn = reinterpret_cast<const unsigned*>(smem + L.binom_off);
-    mc.hinfo = reinterpret_cast<const int*>(smem + L.hinfo_off);
-    double* coef = reinterpret_cast<double*>(smem + L.coef_off);
-    load_coef_c128(a, n, coef);
+    init_ctx(mc, n, m_param, smem, L);
+    load_coef_c128(a, n, smem + L.coef_off);
     __syncthreads();
-    const size_t CW = (size_t)3 * mc.chain_len;
+    const size_t CW = chain_words(kC128, mc.m);
     const size_t layer_words = (size_t)binom_calc(mc.t, mc.t / 2) * CW;
     unsigned long long* dst_region = workspace + (size_t)(s & 1) * layer_words;
     const unsigned long long* src_region = workspace + (size_t)((s + 1) & 1) * layer_words;
     const unsigned nslots = (unsigned)binom_calc(mc.t, s);
     const bool last = (s == mc.t);
     for (unsigned slot = blockIdx.x; slot < nslots; slot += gridDim.x) {
-        const unsigned H = unrank_high(slot, s, mc.t, mc.bn);
-        chain_setup(mc, H, reinterpret_cast<int*>(smem + L.hinfo_off));
+        chain_setup(mc, unrank_high(slot, s, mc.t, mc.bn), reinterpret_cast<int*>(smem + L.hinfo_off));
         __syncthreads();
-        process_chain<KindC128>(mc, H, s, reinterpret_cast<unsigned long long*>(smem + L.chain_off),
-                                src_region, last ? nullptr : dst_region + (size_t)slot * CW, coef,
+        run_chain<kC128, false>(mc, s, smem + L.chain_off, src_region,
+                                last ? nullptr : dst_region + (size_t)slot * CW, smem + L.coef_off,
                                 last, out, out_index);
     }
     if (last && blockIdx.x == 0 && threadIdx.x == 0 && item_status) item_status[out_index] = PERM_OK;
 }
 
+template <bool ZO>
 __global__ void __launch_bounds__(kThreadsInt)
-sz_layer_int(const long long* __restrict__ a, int n, int m, int s, int zero_one,
-             unsigned long long* out, int out_index, int* item_status,
-             unsigned long long* workspace) {
+sz_layer_int(const long long* __restrict__ a, int n, int m_param, int s, unsigned long long* out,
+             int out_index, int* item_status, unsigned long long* workspace) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_width;
     fill_binom(reinterpret_cast<unsigned*>(smem));
-    if (threadIdx.x == 0) s_width = decide_width(a, n, zero_one != 0);
+    if (threadIdx.x == 0) s_width = decide_width(a, n, ZO);
+    const SmemLayout L = smem_layout(kU128, n, sz_low_for(n, m_param));
     MatCtx mc;
-    mc.n = n;
-    mc.m = m;
-    mc.t = n - m;
-    mc.chain_len = 1u << m;
-    const SmemLayout L = smem_layout(1, 2, n, m);
-    mc.bn = reinterpret_cast<const unsigned*>(smem + L.binom_off);
-    mc.hinfo = reinterpret_cast<const int*>(smem + L.hinfo_off);
-    unsigned long long* coef = reinterpret_cast<unsigned long long*>(smem + L.coef_off);
-    load_coef_int(a, n, coef);
+    init_ctx(mc, n, m_param, smem, L);
+    load_coef_int(a, n, reinterpret_cast<unsigned long long*>(smem + L.coef_off));
     __syncthreads();
     const int w = s_width;
-    const int planes = (w == kWidth64) ? 1 : 2;
-    const size_t CW = (size_t)planes * mc.chain_len;
-    // the workspace is sized for two planes; one-plane chains use the same stride
-    const size_t layer_words = (size_t)binom_calc(mc.t, mc.t / 2) * 2 * mc.chain_len;
+    const int kind = (w == kWidth64) ? kU64 : kU128;
+    const size_t CW = chain_words(kind, mc.m);
+    // the workspace is sized for 128-bit chains; 64-bit chains use the same region size
+    const size_t layer_words = (size_t)binom_calc(mc.t, mc.t / 2) * chain_words(kU128, mc.m);
     unsigned long long* dst_region = workspace + (size_t)(s & 1) * layer_words;
     const unsigned long long* src_region = workspace + (size_t)((s + 1) & 1) * layer_words;
     const unsigned nslots = (unsigned)binom_calc(mc.t, s);
     const bool last = (s == mc.t);
     for (unsigned slot = blockIdx.x; slot < nslots; slot += gridDim.x) {
-        const unsigned H = unrank_high(slot, s, mc.t, mc.bn);
-        chain_setup(mc, H, reinterpret_cast<int*>(smem + L.hinfo_off));
+        chain_setup(mc, unrank_high(slot, s, mc.t, mc.bn), reinterpret_cast<int*>(smem + L.hinfo_off));
         __syncthreads();
-        unsigned long long* chain = reinterpret_cast<unsigned long long*>(smem + L.chain_off);
         unsigned long long* dst = last ? nullptr : dst_region + (size_t)slot * CW;
-        if (w == kWidth64)
-            process_chain<KindU64>(mc, H, s, chain, src_region, dst, coef, last, out, out_index);
+        if (kind == kU64)
+            run_chain<kU64, ZO>(mc, s, smem + L.chain_off, src_region, dst, smem + L.coef_off, last, out, out_index);
         else
-            process_chain<KindU128>(mc, H, s, chain, src_region, dst, coef, last, out, out_index);
+            run_chain<kU128, ZO>(mc, s, smem + L.chain_off, src_region, dst, smem + L.coef_off, last, out, out_index);
     }
     if (last && blockIdx.x == 0 && threadIdx.x == 0 && item_status)
         item_status[out_index] = width_status(w);
@@ -644,6 +625,26 @@ __global__ void trivial_kernel(int dtype, const ItemDesc* items, int count, void
     if (item_status) item_status[o] = PERM_OK;
 }
 
+// Kernel selection for the batched integer path.
+typedef void (*int_batched_fn)(const long long*, const ItemDesc*, int, int, unsigned long long*, int*,
+                               unsigned long long*, size_t, unsigned*);
+
+int_batched_fn pick_int_batched(int dtype, int n_max) {
+    const bool zo = dtype == PERM_U01;
+    if (zo && n_max <= 20) return sz_batched_int<true, true>;     // 20! < 2^64
+    if (zo) return sz_batched_int<true, false>;
+    return sz_batched_int<false, false>;
+}
+
+int batched_kind(int dtype, int n_max) {
+    if (dtype == PERM_C128) return kC128;
+    return (dtype == PERM_U01 && n_max <= 20) ? kU64 : kU128;
+}
+
+cudaError_t set_smem(const void* fn, int bytes) {
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -651,9 +652,29 @@ __global__ void trivial_kernel(int dtype, const ItemDesc* items, int count, void
 // ---------------------------------------------------------------------------
 unsigned long long binom_host(int n, int k) { return binom_calc(n, k); }
 
+cudaError_t sz_init_tables() {
+    // once per device: the mask lists, ordered by (popcount, value), for m = 1..kMaxLow
+    static std::mutex mu;
+    static std::vector<int> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> g(mu);
+    if (std::find(done.begin(), done.end(), dev) != done.end()) return cudaSuccess;
+    std::vector<unsigned short> tab;
+    tab.reserve(kMaskTableLen);
+    for (int m = 1; m <= kMaxLow; m++)
+        for (int l = 0; l <= m; l++)
+            for (unsigned x = 0; x < (1u << m); x++)
+                if (__builtin_popcount(x) == l) tab.push_back((unsigned short)x);
+    e = cudaMemcpyToSymbol(g_masks, tab.data(), tab.size() * sizeof(unsigned short));
+    if (e == cudaSuccess) done.push_back(dev);
+    return e;
+}
+
 size_t sz_chain_words(int dtype, int m) {
-    const int planes = dtype == PERM_C128 ? 3 : 2;   // integer chains sized for 128-bit
-    return (size_t)planes << m;
+    // integer chains are sized for 128-bit entries
+    return chain_words(dtype == PERM_C128 ? kC128 : kU128, m);
 }
 
 size_t sz_matrix_workspace_bytes(int dtype, int n, int m_param) {
@@ -663,15 +684,26 @@ size_t sz_matrix_workspace_bytes(int dtype, int n, int m_param) {
     return 2 * (size_t)binom_calc(t, t / 2) * sz_chain_words(dtype, m) * 8;
 }
 
-int sz_smem_bytes(int dtype, int n, int m) {
-    if (dtype == PERM_C128) return smem_layout(3, 3, n, m).total;
-    return smem_layout(1, 2, n, m).total;
+int sz_smem_bytes(int dtype, int n, int m_param) {
+    const int m = sz_low_for(n, m_param);
+    if (dtype == PERM_C128) return smem_layout(kC128, n, m).total;
+    return smem_layout(kU128, n, m).total;
 }
 
 int sz_threads(int dtype) { return dtype == PERM_C128 ? kThreadsC128 : kThreadsInt; }
 
-static cudaError_t set_smem(const void* fn, int bytes) {
-    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+// Resident CTAs per SM of the batched kernel for a batch whose largest order is n_max.
+int sz_batched_occupancy(int dtype, int n_max, int m_param) {
+    const int m = sz_low_for(n_max, m_param);
+    const int kind = batched_kind(dtype, n_max);
+    const int smem = smem_layout(kind, n_max, m).total;
+    const void* fn = dtype == PERM_C128 ? (const void*)sz_batched_c128
+                                        : (const void*)pick_int_batched(dtype, n_max);
+    if (set_smem(fn, smem) != cudaSuccess) return 1;
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, sz_threads(dtype), smem) != cudaSuccess)
+        return 1;
+    return std::max(1, occ);
 }
 
 cudaError_t sz_launch_batched(int dtype, const void* mats, const ItemDesc* items, int count,
@@ -679,7 +711,8 @@ cudaError_t sz_launch_batched(int dtype, const void* mats, const ItemDesc* items
                               size_t ws_per_cta, int grid, unsigned* counter, cudaStream_t st) {
     if (count <= 0) return cudaSuccess;
     const int mm = sz_low_for(n_max, m);
-    const int smem = sz_smem_bytes(dtype, n_max, mm);
+    const int kind = batched_kind(dtype, n_max);
+    const int smem = smem_layout(kind, n_max, mm).total;
     cudaError_t e;
     if (dtype == PERM_C128) {
         e = set_smem((const void*)sz_batched_c128, smem);
@@ -688,12 +721,12 @@ cudaError_t sz_launch_batched(int dtype, const void* mats, const ItemDesc* items
             (const double2*)mats, items, count, m, (double2*)out, item_status,
             (unsigned long long*)workspace, ws_per_cta / 8, counter);
     } else {
-        e = set_smem((const void*)sz_batched_int, smem);
+        int_batched_fn fn = pick_int_batched(dtype, n_max);
+        e = set_smem((const void*)fn, smem);
         if (e != cudaSuccess) return e;
-        sz_batched_int<<<grid, kThreadsInt, smem, st>>>(
-            (const long long*)mats, items, count, m, dtype == PERM_U01 ? 1 : 0,
-            (unsigned long long*)out, item_status, (unsigned long long*)workspace,
-            ws_per_cta / 8, counter);
+        fn<<<grid, kThreadsInt, smem, st>>>((const long long*)mats, items, count, m,
+                                            (unsigned long long*)out, item_status,
+                                            (unsigned long long*)workspace, ws_per_cta / 8, counter);
     }
     return cudaGetLastError();
 }
@@ -703,21 +736,25 @@ cudaError_t sz_launch_single(int dtype, const void* mats, long long offset, int 
                              int grid_cap, cudaStream_t st) {
     const int mm = sz_low_for(n, m);
     const int t = n - mm;
-    const int smem = sz_smem_bytes(dtype, n, mm);
-    cudaError_t e;
-    if (dtype == PERM_C128) e = set_smem((const void*)sz_layer_c128, smem);
-    else e = set_smem((const void*)sz_layer_int, smem);
+    const int smem = sz_smem_bytes(dtype, n, m);
+    const void* fn = dtype == PERM_C128 ? (const void*)sz_layer_c128
+                   : (dtype == PERM_U01 ? (const void*)sz_layer_int<true> : (const void*)sz_layer_int<false>);
+    cudaError_t e = set_smem(fn, smem);
     if (e != cudaSuccess) return e;
     for (int s = 0; s <= t; s++) {
         const int grid = (int)std::min<unsigned long long>(binom_calc(t, s), (unsigned long long)grid_cap);
         if (dtype == PERM_C128) {
             sz_layer_c128<<<grid, kThreadsC128, smem, st>>>(
-                (const double2*)mats + offset, n, mm, s, (double2*)out, out_index, item_status,
+                (const double2*)mats + offset, n, m, s, (double2*)out, out_index, item_status,
                 (unsigned long long*)workspace);
+        } else if (dtype == PERM_U01) {
+            sz_layer_int<true><<<grid, kThreadsInt, smem, st>>>(
+                (const long long*)mats + offset, n, m, s, (unsigned long long*)out, out_index,
+                item_status, (unsigned long long*)workspace);
         } else {
-            sz_layer_int<<<grid, kThreadsInt, smem, st>>>(
-                (const long long*)mats + offset, n, mm, s, dtype == PERM_U01 ? 1 : 0,
-                (unsigned long long*)out, out_index, item_status, (unsigned long long*)workspace);
+            sz_layer_int<false><<<grid, kThreadsInt, smem, st>>>(
+                (const long long*)mats + offset, n, m, s, (unsigned long long*)out, out_index,
+                item_status, (unsigned long long*)workspace);
         }
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
