@@ -46,6 +46,11 @@ def parse():
     ap.add_argument("--count", type=int, default=COUNT)
     ap.add_argument("--no-extras", action="store_true", help="skip plain / n=32 / serving measurements")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--case", default="bench", choices=["bench", "single"],
+                    help="single: one matrix of order --n with --method (for profiling)")
+    ap.add_argument("--n", type=int, default=32)
+    ap.add_argument("--method", default="sz", choices=["sz", "ryser"])
+    ap.add_argument("--dtype", default="c128", choices=["c128", "u01"])
     return ap.parse_args()
 
 
@@ -103,6 +108,24 @@ class Clocks:
         return {"sm_mhz": float(np.median(sm)) if sm else None,
                 "sm_max_mhz": float(max(smax)) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# multi-GPU replicas: max-over-ranks time and the whole-job rate
+# ---------------------------------------------------------------------------
+def max_over_ranks(x: float, dist=None, device=None) -> float:
+    """The largest value of x over all ranks (x itself without a process group)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: int, world: int, seconds: float) -> float:
+    """Units all replicas processed divided by the slowest replica's time."""
+    return world * units_per_rank / seconds
 
 
 # ---------------------------------------------------------------------------
@@ -240,13 +263,9 @@ def run_gpu(args, rank, world):
     step_ms = [a.elapsed_time(c) for a, b, c in ev]
     c_ms = [a.elapsed_time(b) for a, b, c in ev]
     i_ms = [b.elapsed_time(c) for a, b, c in ev]
-    total_ms = float(np.sum(step_ms))
-    if dist:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(float(np.sum(step_ms)), dist, "cuda")
     ms_per_step = total_ms / args.steps
-    value = world * 2 * count / (ms_per_step / 1000.0)
+    value = whole_job_rate(2 * count, world, ms_per_step / 1000.0)
 
     # ---- e2e: host buffers through perm_batch_host, copies inside the timed region ----
     ch_np = np.ascontiguousarray(cm).reshape(-1)
@@ -264,12 +283,8 @@ def run_gpu(args, rank, world):
     for _ in range(args.steps):
         pc.batch_host(ch_pin, sizes, co, None, stream)
         pi.batch_host(ih_pin, sizes, io, None, stream)
-    e2e_s = (time.perf_counter() - t0) / args.steps
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": world * 2 * count / e2e_s, "unit": UNIT,
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, dist, "cuda")
+    e2e = {"value": whole_job_rate(2 * count, world, e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": int(ch_np.nbytes + ih_np.nbytes), "d2h_bytes_per_step": int(count * 16 * 2)}
 
     if rank != 0:
@@ -359,10 +374,41 @@ def measure_extras(lp, torch, cm, im, stream, c_kernel_ms, count):
     return out
 
 
+def run_single(args):
+    """One matrix of order n through one method, timed twice (the second run reported)."""
+    import torch
+    from paper_1802_02779_gb300 import build, libperm as lp, workloads as wl
+    build.build()
+    if args.dtype == "c128":
+        a = wl.gaussian_complex(args.n, wl.SEED_BASE + 5, scale=1.0 / args.n)
+        dev = torch.from_numpy(a.reshape(-1)).cuda()
+        out = torch.empty(1, dtype=torch.complex128, device="cuda")
+    else:
+        a = wl.bernoulli01(1, args.n, 0.5, wl.SEED_BASE + 4)[0]
+        dev = torch.from_numpy(a.reshape(-1)).cuda()
+        out = torch.empty((1, 2), dtype=torch.int64, device="cuda")
+    meth = lp.METHOD_SZ if args.method == "sz" else lp.METHOD_RYSER
+    stream = torch.cuda.current_stream()
+    times = []
+    with lp.Plan(args.n, args.dtype, method=meth, max_batch=1) as p:
+        for _ in range(2):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            p.batch(dev, [args.n], out, None, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+    print(json.dumps({"case": "single", "n": args.n, "method": args.method, "dtype": args.dtype,
+                      "ms": times[-1], "value": str(out.cpu().numpy().tolist())}))
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.case == "single":
+        run_single(args)
+        return
     if args.impl == "reference":
         run_reference(args, rank, world)
     else:

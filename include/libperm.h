@@ -95,7 +95,7 @@ typedef struct perm_opts {
     int method;               /* perm_method */
     unsigned flags;           /* PERM_FLAG_* */
     int ctas_per_sm;          /* persistent CTAs per SM for batched launches; 0 = tuned */
-    int low_cols;             /* Store-zechin low-column count m, 1..13 (shared-memory chain width); 0 = 12 */
+    int low_cols;             /* Store-zechin low-column count m, 1..13 (shared-memory chain width); 0 = 12 batched, 13 single */
 } perm_opts;
 
 typedef struct perm_plan_s *perm_plan_t;
@@ -131,7 +131,8 @@ perm_status perm_batch(perm_plan_t plan, const void *mats, const int *sizes, int
 perm_status perm_batch_host(perm_plan_t plan, const void *mats, const int *sizes, int count,
                             void *out, int *item_status, void *stream);
 
-/* Continuous-batching server (one device, one stream).  Requests of any n and
+/* Continuous-batching server (one device; the server owns its streams, and
+   `stream` is ignored).  Requests of any n and
    dtype are admitted while their Store-zechin tables fit the memory budget
    (otherwise they run with Ryser), batched with whatever else is waiting, and
    completed asynchronously.
@@ -140,7 +141,13 @@ perm_status perm_batch_host(perm_plan_t plan, const void *mats, const int *sizes
      perm_poll returns PERM_EAGAIN until the ticket is done, then writes the 16
        result bytes (double2, or (low, high) uint64) and the item status.
      perm_server_destroy stops the server; PERM_ETIMEDOUT if in-flight work
-       does not finish within timeout_ms. */
+       does not finish within timeout_ms (the server is then left to drain in
+       the background and its memory is not freed).
+   Server options: mem_budget_bytes = Store-zechin table budget of the large
+   lane (0 = min(80 GB, a third of the free memory)); max_batch = queue
+   capacity (0 = 65536); the other fields are ignored.  Orders n <= 20 are
+   batched together; larger orders run one at a time, with Store-zechin when
+   their tables fit the budget and with Ryser otherwise. */
 perm_status perm_server_create(const perm_opts *opts, void *stream, perm_server_t *out);
 perm_status perm_submit(perm_server_t server, const void *host_mat, int n, perm_dtype dtype,
                         uint64_t *ticket);

@@ -30,7 +30,8 @@ struct perm_plan_s {
     unsigned flags = 0;
     int max_batch = 65536;
     int num_sms = 0;
-    int m_low = 12;
+    int m_low = 12;               // chain width of the batched kernel (two CTAs per SM)
+    int m_single = 13;            // chain width of the one-matrix-over-the-GPU path
     size_t budget = 0;
 
     // Store-zechin
@@ -136,6 +137,7 @@ perm_status plan_create_impl(int n_max, perm_dtype dtype, const perm_opts* opts,
     p->flags = o.flags;
     p->max_batch = o.max_batch ? o.max_batch : 65536;
     p->m_low = o.low_cols ? o.low_cols : 12;
+    p->m_single = o.low_cols ? o.low_cols : 13;
     cudaError_t e = cudaGetDevice(&p->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
     size_t free_b = 0, total_b = 0;
@@ -156,11 +158,11 @@ perm_status plan_create_impl(int n_max, perm_dtype dtype, const perm_opts* opts,
         sz_batched = p->sz_ws_per_cta * (size_t)p->sz_grid;
         // largest n whose single-matrix workspace fits the remaining budget
         for (int n = 1; n <= std::min(n_max, kMaxNSZ); n++) {
-            const size_t need = sz_matrix_workspace_bytes(dtype, n, p->m_low);
+            const size_t need = sz_matrix_workspace_bytes(dtype, n, p->m_single);
             if (need + (size_t)(1 << 20) <= p->budget) p->sz_single_nmax = n;
         }
         if (p->sz_single_nmax > 0)
-            sz_single = sz_matrix_workspace_bytes(dtype, p->sz_single_nmax, p->m_low);
+            sz_single = sz_matrix_workspace_bytes(dtype, p->sz_single_nmax, p->m_single);
         if (sz_batched > p->budget) {   // shrink the persistent grid to the budget
             p->sz_grid = (int)std::max<size_t>(1, p->budget / std::max<size_t>(1, p->sz_ws_per_cta));
             sz_batched = p->sz_ws_per_cta * (size_t)p->sz_grid;
@@ -308,7 +310,7 @@ perm_status perm_batch(perm_plan_t p, const void* mats, const int* sizes, int co
         if (e != cudaSuccess) return PERM_ECUDA;
     }
     for (auto& d : szs) {
-        e = sz_launch_single(p->dtype, mats, d.offset, d.n, p->m_low, d.out_index, out, item_status,
+        e = sz_launch_single(p->dtype, mats, d.offset, d.n, p->m_single, d.out_index, out, item_status,
                              p->ws, p->num_sms, st);
         if (e != cudaSuccess) return PERM_ECUDA;
     }

@@ -89,6 +89,7 @@ struct perm_server_s {
     std::thread worker;
     Lane lanes[2];
     size_t table_budget = 0;
+    int queue_cap = kQueueCap;
 };
 
 namespace {
@@ -132,6 +133,7 @@ perm_plan_t lane_plan(perm_server_t s, Lane& L, int dtype, bool large) {
         o.flags = 0;
         o.method = PERM_METHOD_AUTO;
         o.max_batch = large ? 1 : kLaneBatch;
+        if (!large) o.mem_budget_bytes = 0;   // the table budget applies to the large lane
         perm_plan_t p = nullptr;
         perm_status st;
         if (large)
@@ -276,6 +278,7 @@ perm_status perm_server_create(const perm_opts* opts, void* stream, perm_server_
     perm_server_t s = new (std::nothrow) perm_server_s();
     if (!s) return PERM_ENOMEM;
     if (opts) s->opts = *opts;
+    if (s->opts.max_batch > 0) s->queue_cap = s->opts.max_batch;
     // table budget for the large lane: default 20 GB (or what is free)
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) { delete s; return PERM_ECUDA; }
@@ -317,7 +320,7 @@ perm_status perm_submit(perm_server_t s, const void* host_mat, int n, perm_dtype
     if (bytes) std::memcpy(r->mat.data(), host_mat, bytes);
     {
         std::lock_guard<std::mutex> g(s->mu);
-        if (s->queued >= kQueueCap) return PERM_EAGAIN;
+        if (s->queued >= s->queue_cap) return PERM_EAGAIN;
         r->ticket = s->next_ticket++;
         *ticket = r->ticket;
         Request* raw = r.get();

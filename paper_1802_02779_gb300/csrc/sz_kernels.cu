@@ -60,8 +60,9 @@ namespace perm {
 namespace {
 
 constexpr int kBinomDim = 24;            // C(x, y) for x < 24 (t <= 21, m <= 13)
-constexpr int kThreadsC128 = 256;
-constexpr int kThreadsInt = 512;
+constexpr int kThreadsC128 = 384;         // batched: two CTAs per SM
+constexpr int kThreadsC128Single = 512;   // one matrix over the whole GPU: one CTA per SM
+constexpr int kThreadsInt = 256;          // integers: up to four CTAs per SM
 constexpr int kMaskTableLen = (2 << kMaxLow) - 2;   // sum_{m=1..13} 2^m
 
 // masks of all subsets of {0..m-1}, ordered by (popcount, value); the table
@@ -89,6 +90,7 @@ __host__ __device__ inline int coef_bytes(int kind, int n) {
 struct SmemLayout {
     int binom_off;      // unsigned[kBinomDim][kBinomDim + 1]
     int hinfo_off;      // int[2 * kBinomDim]: predecessor slot, column
+    int rowmask_off;    // unsigned[kMaxN]: low columns with a nonzero entry, per row (integers)
     int coef_off;       // C128: double2 xy[n*n] then double s[n*n]; ints: u64[n*n]
     int chain_off;      // C128: double2 uv[2^m] then double w[2^m]; u64[2^m]; ulonglong2[2^m]
     int total;
@@ -100,7 +102,8 @@ __host__ __device__ inline SmemLayout smem_layout(int kind, int n, int m) {
     SmemLayout s;
     s.binom_off = 0;
     s.hinfo_off = align16(s.binom_off + kBinomDim * (kBinomDim + 1) * 4);
-    s.coef_off = align16(s.hinfo_off + 2 * kBinomDim * 4);
+    s.rowmask_off = align16(s.hinfo_off + 2 * kBinomDim * 4);
+    s.coef_off = align16(s.rowmask_off + kMaxN * 4);
     s.chain_off = align16(s.coef_off + coef_bytes(kind, n));
     s.total = align16(s.chain_off + chain_bytes_smem(kind, m));
     return s;
@@ -128,6 +131,7 @@ struct MatCtx {
     const unsigned* bn;          // smem binomials
     const int* hinfo;            // smem: [0..s) predecessor slots, [kBinomDim..) columns
     const unsigned short* masks; // mask list of this m (global)
+    const unsigned* rowmask;     // smem: per row, the low columns with a nonzero entry
 };
 
 // Predecessor info for chain H: for the p-th high element h_p (ascending),
@@ -155,6 +159,7 @@ __device__ __forceinline__ void chain_setup(const MatCtx& mc, unsigned Hmask, in
 // complex128 chain.  gprev: previous layer region (chains of 3*CL doubles:
 // uv plane then w plane); gdst: this chain's slot or null.
 // ---------------------------------------------------------------------------
+template <bool PIPE>
 __device__ void chain_c128(const MatCtx& mc, int s, unsigned char* chain_smem, const double* gprev,
                            double* gdst, const unsigned char* coef_smem, bool last, double2* out,
                            int out_index) {
@@ -233,23 +238,28 @@ __device__ void chain_c128(const MatCtx& mc, int s, unsigned char* chain_smem, c
                     P2 = __fma_rn(c.y, p.y, P2);
                     P3 = __fma_rn(rs[j], pw, P3);
                 }
+                // high terms in groups of four; with PIPE the next group's loads are
+                // issued before the current group's FMAs (long chains of high terms)
+                for (int q = 0; q < s; q += 4) {
+                    double2 nuv[4];
+                    double nw[4];
+                    if (PIPE) {
 #pragma unroll
-                for (int z = 0; z < 4; z++) {
-                    if (z < s) {
-                        const int col = hcol[z];
-                        const double2 c = rxy[col];
-                        P1 = __fma_rn(c.x, huv[z].x, P1);
-                        P2 = __fma_rn(c.y, huv[z].y, P2);
-                        P3 = __fma_rn(rs[col], hw[z], P3);
-                    }
-                }
-                for (int q = 4; q < s; q += 4) {
+                        for (int z = 0; z < 4; z++) {
+                            if (q + 4 + z < s) {
+                                const double* pc = gprev + (size_t)hslot[q + 4 + z] * 3 * CL;
+                                nuv[z] = __ldg(reinterpret_cast<const double2*>(pc) + idx);
+                                nw[z] = __ldg(pc + 2 * CL + idx);
+                            }
+                        }
+                    } else if (q > 0) {
 #pragma unroll
-                    for (int z = 0; z < 4; z++) {
-                        if (q + z < s) {
-                            const double* pc = gprev + (size_t)hslot[q + z] * 3 * CL;
-                            huv[z] = __ldg(reinterpret_cast<const double2*>(pc) + idx);
-                            hw[z] = __ldg(pc + 2 * CL + idx);
+                        for (int z = 0; z < 4; z++) {
+                            if (q + z < s) {
+                                const double* pc = gprev + (size_t)hslot[q + z] * 3 * CL;
+                                huv[z] = __ldg(reinterpret_cast<const double2*>(pc) + idx);
+                                hw[z] = __ldg(pc + 2 * CL + idx);
+                            }
                         }
                     }
 #pragma unroll
@@ -262,10 +272,16 @@ __device__ void chain_c128(const MatCtx& mc, int s, unsigned char* chain_smem, c
                             P3 = __fma_rn(rs[col], hw[z], P3);
                         }
                     }
+                    if (PIPE) {
+#pragma unroll
+                        for (int z = 0; z < 4; z++) { huv[z] = nuv[z]; hw[z] = nw[z]; }
+                    }
                 }
-                u = __dsub_rn(P1, P2);
-                v = __dsub_rn(__dsub_rn(P3, P1), P2);
-                w = __dadd_rn(u, v);
+                // Re = P1 - P2, Im = (P3 - P1) - P2, w = Re + Im, each a single
+                // rounding; written as FMAs with +-1 (same results, faster pipe issue)
+                u = __fma_rn(P2, -1.0, P1);
+                v = __fma_rn(P2, -1.0, __fma_rn(P1, -1.0, P3));
+                w = __fma_rn(u, 1.0, v);
             }
             suv[mask] = make_double2(u, v);
             sw[mask] = w;
@@ -330,19 +346,17 @@ __device__ void chain_int(const MatCtx& mc, int s, unsigned char* chain_smem,
                         }
                     }
                 }
-                unsigned mm = mask;
+                // low terms: only the columns of L whose coefficient is nonzero
+                unsigned mm = mask & mc.rowmask[k - 1];
                 while (mm) {
                     const int j = __ffs(mm) - 1;
                     mm &= mm - 1;
-                    const unsigned long long c = rc[j];
-                    if (c) {
-                        const unsigned pm = mask ^ (1u << j);
-                        if (W128) {
-                            const ulonglong2 p = sv2[pm];
-                            val = ZO ? u128_add2(val, p.x, p.y) : u128_mac(val, c, p.x, p.y);
-                        } else {
-                            val.lo += ZO ? sv[pm] : c * sv[pm];
-                        }
+                    const unsigned pm = mask ^ (1u << j);
+                    if (W128) {
+                        const ulonglong2 p = sv2[pm];
+                        val = ZO ? u128_add2(val, p.x, p.y) : u128_mac(val, rc[j], p.x, p.y);
+                    } else {
+                        val.lo += ZO ? sv[pm] : rc[j] * sv[pm];
                     }
                 }
                 for (int q = 0; q < s; q += 4) {
@@ -417,11 +431,18 @@ __device__ inline void load_coef_c128(const double2* a, int n, unsigned char* co
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
         const double2 z = a[e];
         xy[e] = z;
-        sm[e] = __dadd_rn(z.x, z.y);
+        sm[e] = __fma_rn(z.x, 1.0, z.y);
     }
 }
-__device__ inline void load_coef_int(const long long* a, int n, unsigned long long* coef) {
+__device__ inline void load_coef_int(const long long* a, int n, int m, unsigned long long* coef,
+                                     unsigned* rowmask) {
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) coef[e] = (unsigned long long)a[e];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        unsigned rm = 0;
+        for (int j = 0; j < m; j++)
+            if (a[(size_t)i * n + j] != 0) rm |= 1u << j;
+        rowmask[i] = rm;
+    }
 }
 
 __device__ inline void init_ctx(MatCtx& mc, int n, int m_param, const unsigned char* smem,
@@ -433,6 +454,7 @@ __device__ inline void init_ctx(MatCtx& mc, int n, int m_param, const unsigned c
     mc.bn = reinterpret_cast<const unsigned*>(smem + L.binom_off);
     mc.hinfo = reinterpret_cast<const int*>(smem + L.hinfo_off);
     mc.masks = g_masks + ((1 << mc.m) - 2);
+    mc.rowmask = reinterpret_cast<const unsigned*>(smem + L.rowmask_off);
 }
 
 // Global-memory words of one chain.
@@ -441,13 +463,13 @@ __host__ __device__ inline size_t chain_words(int kind, int m) {
 }
 
 // One chain of a matrix, any element kind.
-template <int KIND, bool ZO>
+template <int KIND, bool ZO, bool PIPE = false>
 __device__ __forceinline__ void run_chain(const MatCtx& mc, int s, unsigned char* smem_chain,
                                           const unsigned long long* src, unsigned long long* dst,
                                           const unsigned char* coef, bool last, void* out,
                                           int out_index) {
     if (KIND == kC128)
-        chain_c128(mc, s, smem_chain, reinterpret_cast<const double*>(src),
+        chain_c128<PIPE>(mc, s, smem_chain, reinterpret_cast<const double*>(src),
                    reinterpret_cast<double*>(dst), coef, last, reinterpret_cast<double2*>(out),
                    out_index);
     else
@@ -513,7 +535,7 @@ sz_batched_c128(const double2* __restrict__ mats, const ItemDesc* __restrict__ i
 // W64ONLY: the host guarantees every item fits 64 bits (0/1 input, n <= 20),
 // so the chain needs only one word per entry.
 template <bool ZO, bool W64ONLY>
-__global__ void __launch_bounds__(kThreadsInt)
+__global__ void __launch_bounds__(kThreadsInt, 3)
 sz_batched_int(const long long* __restrict__ mats, const ItemDesc* __restrict__ items, int count,
                int m_param, unsigned long long* out, int* item_status,
                unsigned long long* workspace, size_t ws_words_per_cta, unsigned* counter) {
@@ -534,7 +556,7 @@ sz_batched_int(const long long* __restrict__ mats, const ItemDesc* __restrict__ 
         MatCtx mc;
         init_ctx(mc, n, m_param, smem, L);
         unsigned long long* coef = reinterpret_cast<unsigned long long*>(smem + L.coef_off);
-        load_coef_int(mats + d.offset, n, coef);
+        load_coef_int(mats + d.offset, n, mc.m, coef, reinterpret_cast<unsigned*>(smem + L.rowmask_off));
         __syncthreads();
         const int w = s_width;
         unsigned long long* ws = workspace + (size_t)blockIdx.x * ws_words_per_cta;
@@ -550,7 +572,7 @@ sz_batched_int(const long long* __restrict__ mats, const ItemDesc* __restrict__ 
 // ---------------------------------------------------------------------------
 // Single-matrix kernels: one launch per layer s; CTAs stride over the slots.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreadsC128, 2)
+__global__ void __launch_bounds__(kThreadsC128Single, 1)
 sz_layer_c128(const double2* __restrict__ a, int n, int m_param, int s, double2* out, int out_index,
               int* item_status, unsigned long long* workspace) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -569,15 +591,15 @@ sz_layer_c128(const double2* __restrict__ a, int n, int m_param, int s, double2*
     for (unsigned slot = blockIdx.x; slot < nslots; slot += gridDim.x) {
         chain_setup(mc, unrank_high(slot, s, mc.t, mc.bn), reinterpret_cast<int*>(smem + L.hinfo_off));
         __syncthreads();
-        run_chain<kC128, false>(mc, s, smem + L.chain_off, src_region,
-                                last ? nullptr : dst_region + (size_t)slot * CW, smem + L.coef_off,
-                                last, out, out_index);
+        run_chain<kC128, false, true>(mc, s, smem + L.chain_off, src_region,
+                                      last ? nullptr : dst_region + (size_t)slot * CW, smem + L.coef_off,
+                                      last, out, out_index);
     }
     if (last && blockIdx.x == 0 && threadIdx.x == 0 && item_status) item_status[out_index] = PERM_OK;
 }
 
 template <bool ZO>
-__global__ void __launch_bounds__(kThreadsInt)
+__global__ void __launch_bounds__(kThreadsInt, 3)
 sz_layer_int(const long long* __restrict__ a, int n, int m_param, int s, unsigned long long* out,
              int out_index, int* item_status, unsigned long long* workspace) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -587,7 +609,8 @@ sz_layer_int(const long long* __restrict__ a, int n, int m_param, int s, unsigne
     const SmemLayout L = smem_layout(kU128, n, sz_low_for(n, m_param));
     MatCtx mc;
     init_ctx(mc, n, m_param, smem, L);
-    load_coef_int(a, n, reinterpret_cast<unsigned long long*>(smem + L.coef_off));
+    load_coef_int(a, n, mc.m, reinterpret_cast<unsigned long long*>(smem + L.coef_off),
+                  reinterpret_cast<unsigned*>(smem + L.rowmask_off));
     __syncthreads();
     const int w = s_width;
     const int kind = (w == kWidth64) ? kU64 : kU128;
@@ -744,7 +767,7 @@ cudaError_t sz_launch_single(int dtype, const void* mats, long long offset, int 
     for (int s = 0; s <= t; s++) {
         const int grid = (int)std::min<unsigned long long>(binom_calc(t, s), (unsigned long long)grid_cap);
         if (dtype == PERM_C128) {
-            sz_layer_c128<<<grid, kThreadsC128, smem, st>>>(
+            sz_layer_c128<<<grid, kThreadsC128Single, smem, st>>>(
                 (const double2*)mats + offset, n, m, s, (double2*)out, out_index, item_status,
                 (unsigned long long*)workspace);
         } else if (dtype == PERM_U01) {

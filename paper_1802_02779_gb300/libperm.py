@@ -209,3 +209,87 @@ def permanents(mats, dtype: Optional[str] = None, method: int = METHOD_AUTO, fla
             plan.close()
     res = o if dtype == "c128" else [u128_to_int(r) for r in o]
     return (res, s) if return_status else res
+
+
+class Server:
+    """The continuous-batching server (perm_server_*): submit host matrices, poll results."""
+
+    def __init__(self, mem_budget_bytes: int = 0, max_batch: int = 0):
+        lib = load()
+        opts = PermOpts(mem_budget_bytes, max_batch, METHOD_AUTO, 0, 0, 0)
+        h = _VP()
+        _check(lib.perm_server_create(ctypes.byref(opts), None, ctypes.byref(h)), "perm_server_create")
+        self._h = h
+        self._keep = {}
+
+    def try_submit(self, mat, dtype: str):
+        """Submit one matrix; returns (True, ticket) or (False, None) when the queue is full."""
+        a = np.ascontiguousarray(mat, dtype=np.complex128 if dtype == "c128" else np.int64)
+        t = ctypes.c_uint64()
+        rc = load().perm_submit(self._h, _VP(a.ctypes.data if a.size else 0), int(a.shape[0]),
+                                DTYPES[dtype], ctypes.byref(t))
+        if rc == PERM_EAGAIN:
+            return False, None
+        _check(rc, "perm_submit")
+        self._keep[t.value] = dtype
+        return True, t.value
+
+    def submit(self, mat, dtype: str) -> int:
+        while True:
+            ok, t = self.try_submit(mat, dtype)
+            if ok:
+                return t
+
+    def poll(self, ticket: int):
+        """('done', (value, status)), ('pending', None) or ('missing', None)."""
+        buf = (ctypes.c_uint64 * 2)()
+        st = ctypes.c_int()
+        rc = load().perm_poll(self._h, ctypes.c_uint64(ticket), buf, ctypes.byref(st))
+        if rc == PERM_EAGAIN:
+            return "pending", None
+        if rc == PERM_ENOTFOUND:
+            return "missing", None
+        _check(rc, "perm_poll")
+        dtype = self._keep.pop(ticket, "c128")
+        if dtype == "c128":
+            v = np.frombuffer(bytes(buf), dtype=np.complex128)[0]
+        else:
+            v = u128_to_int((buf[0], buf[1]))
+        return "done", (v, st.value)
+
+    def wait_all(self, tickets, timeout_s: float = 60.0, sleep_s: float = 0.0002):
+        import time as _t
+        out = {}
+        end = _t.monotonic() + timeout_s
+        pending = list(tickets)
+        while pending:
+            rest = []
+            for t in pending:
+                state, v = self.poll(t)
+                if state == "done":
+                    out[t] = v
+                elif state == "pending":
+                    rest.append(t)
+                else:
+                    raise LibpermError(PERM_ENOTFOUND, "perm_poll")
+            pending = rest
+            if pending:
+                if _t.monotonic() > end:
+                    raise TimeoutError(f"{len(pending)} requests not done")
+                _t.sleep(sleep_s)
+        return [out[t] for t in tickets]
+
+    def destroy(self, timeout_ms: int = 600000) -> int:
+        rc = PERM_OK
+        if getattr(self, "_h", None) and self._h.value:
+            rc = load().perm_server_destroy(self._h, int(timeout_ms))
+            self._h = _VP()
+        return rc
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        rc = self.destroy()
+        if rc != PERM_OK:
+            raise LibpermError(rc, "perm_server_destroy")
