@@ -14,6 +14,7 @@
 #include "perm_internal.cuh"
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -32,6 +33,7 @@ struct perm_plan_s {
     int num_sms = 0;
     int m_low = 12;               // chain width of the batched kernel (two CTAs per SM)
     int m_single = 13;            // chain width of the one-matrix-over-the-GPU path
+    int c128_threads = 384;       // CTA size of the batched complex kernel
     size_t budget = 0;
 
     // Store-zechin
@@ -138,6 +140,9 @@ perm_status plan_create_impl(int n_max, perm_dtype dtype, const perm_opts* opts,
     p->max_batch = o.max_batch ? o.max_batch : 65536;
     p->m_low = o.low_cols ? o.low_cols : 12;
     p->m_single = o.low_cols ? o.low_cols : 13;
+    // experiment knobs (results are bit-identical for every choice)
+    if (const char* v = getenv("LIBPERM_SZ_LOW")) { int x = atoi(v); if (x >= 1 && x <= kMaxLow) p->m_low = x; }
+    if (const char* v = getenv("LIBPERM_SZ_THREADS")) { int x = atoi(v); if (sz_c128_threads_valid(x)) p->c128_threads = x; }
     cudaError_t e = cudaGetDevice(&p->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
     size_t free_b = 0, total_b = 0;
@@ -153,7 +158,8 @@ perm_status plan_create_impl(int n_max, perm_dtype dtype, const perm_opts* opts,
         p->sz_ws_per_cta = sz_matrix_workspace_bytes(dtype, p->sz_batch_nmax, p->m_low);
         if (sz_init_tables() != cudaSuccess) { delete p; return PERM_ECUDA; }
         int per_sm = o.ctas_per_sm ? o.ctas_per_sm
-                                   : sz_batched_occupancy(dtype, std::max(1, p->sz_batch_nmax), p->m_low);
+                                   : sz_batched_occupancy(dtype, std::max(1, p->sz_batch_nmax), p->m_low,
+                                                          p->c128_threads);
         p->sz_grid = p->num_sms * per_sm;
         sz_batched = p->sz_ws_per_cta * (size_t)p->sz_grid;
         // largest n whose single-matrix workspace fits the remaining budget
@@ -306,7 +312,8 @@ perm_status perm_batch(perm_plan_t p, const void* mats, const int* sizes, int co
         if (e != cudaSuccess) return PERM_ECUDA;
         const int grid = std::min<int>(p->sz_grid, (int)szb.size());
         e = sz_launch_batched(p->dtype, mats, dd + szb_at, (int)szb.size(), szb.front().n, p->m_low,
-                              out, item_status, p->ws, p->sz_ws_per_cta, grid, p->d_counter, st);
+                              p->c128_threads, out, item_status, p->ws, p->sz_ws_per_cta, grid,
+                              p->d_counter, st);
         if (e != cudaSuccess) return PERM_ECUDA;
     }
     for (auto& d : szs) {

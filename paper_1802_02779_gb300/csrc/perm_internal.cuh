@@ -142,14 +142,16 @@ size_t sz_chain_words(int dtype, int m);                 // 64-bit words per cha
 size_t sz_matrix_workspace_bytes(int dtype, int n, int m);
 int sz_smem_bytes(int dtype, int n, int m);                // dynamic shared memory per CTA
 int sz_threads(int dtype);
-int sz_batched_occupancy(int dtype, int n_max, int m);     // resident CTAs per SM
+int sz_batched_occupancy(int dtype, int n_max, int m, int threads);   // resident CTAs per SM
+int sz_c128_threads_valid(int threads);
 cudaError_t sz_init_tables();                              // once per device (idempotent)
 
 // Batched: one CTA per matrix, persistent over `count` items (dynamic order by
 // an atomic counter at *counter, which must be zero at launch).
 cudaError_t sz_launch_batched(int dtype, const void* mats, const ItemDesc* items, int count,
-                              int n_max, int m, void* out, int* item_status, void* workspace,
-                              size_t ws_per_cta, int grid, unsigned* counter, cudaStream_t st);
+                              int n_max, int m, int threads, void* out, int* item_status,
+                              void* workspace, size_t ws_per_cta, int grid, unsigned* counter,
+                              cudaStream_t st);
 
 // One matrix, all CTAs on the chains of one layer at a time (t+1 launches).
 cudaError_t sz_launch_single(int dtype, const void* mats, long long offset, int n, int m,

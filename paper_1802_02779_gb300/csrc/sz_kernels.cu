@@ -504,7 +504,8 @@ __device__ void run_matrix_cta(const MatCtx& mc, unsigned char* smem_chain, unsi
 // ---------------------------------------------------------------------------
 // Batched kernels: one CTA per matrix, persistent over the item list.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreadsC128, 2)
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS, THREADS <= 384 ? 2 : 1)
 sz_batched_c128(const double2* __restrict__ mats, const ItemDesc* __restrict__ items, int count,
                 int m_param, double2* out, int* item_status, unsigned long long* workspace,
                 size_t ws_words_per_cta, unsigned* counter) {
@@ -715,34 +716,54 @@ int sz_smem_bytes(int dtype, int n, int m_param) {
 
 int sz_threads(int dtype) { return dtype == PERM_C128 ? kThreadsC128 : kThreadsInt; }
 
+// Batched complex kernel variants by CTA size.
+static const void* c128_batched_fn(int threads) {
+    switch (threads) {
+        case 256: return (const void*)sz_batched_c128<256>;
+        case 512: return (const void*)sz_batched_c128<512>;
+        default: return (const void*)sz_batched_c128<384>;
+    }
+}
+int sz_c128_threads_valid(int threads) { return threads == 256 || threads == 384 || threads == 512; }
+
 // Resident CTAs per SM of the batched kernel for a batch whose largest order is n_max.
-int sz_batched_occupancy(int dtype, int n_max, int m_param) {
+int sz_batched_occupancy(int dtype, int n_max, int m_param, int threads) {
     const int m = sz_low_for(n_max, m_param);
     const int kind = batched_kind(dtype, n_max);
     const int smem = smem_layout(kind, n_max, m).total;
-    const void* fn = dtype == PERM_C128 ? (const void*)sz_batched_c128
+    const void* fn = dtype == PERM_C128 ? c128_batched_fn(threads)
                                         : (const void*)pick_int_batched(dtype, n_max);
+    const int nthr = dtype == PERM_C128 ? threads : kThreadsInt;
     if (set_smem(fn, smem) != cudaSuccess) return 1;
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, sz_threads(dtype), smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, nthr, smem) != cudaSuccess)
         return 1;
     return std::max(1, occ);
 }
 
 cudaError_t sz_launch_batched(int dtype, const void* mats, const ItemDesc* items, int count,
-                              int n_max, int m, void* out, int* item_status, void* workspace,
-                              size_t ws_per_cta, int grid, unsigned* counter, cudaStream_t st) {
+                              int n_max, int m, int threads, void* out, int* item_status,
+                              void* workspace, size_t ws_per_cta, int grid, unsigned* counter,
+                              cudaStream_t st) {
     if (count <= 0) return cudaSuccess;
     const int mm = sz_low_for(n_max, m);
     const int kind = batched_kind(dtype, n_max);
     const int smem = smem_layout(kind, n_max, mm).total;
     cudaError_t e;
     if (dtype == PERM_C128) {
-        e = set_smem((const void*)sz_batched_c128, smem);
+        const void* fn = c128_batched_fn(threads);
+        e = set_smem(fn, smem);
         if (e != cudaSuccess) return e;
-        sz_batched_c128<<<grid, kThreadsC128, smem, st>>>(
-            (const double2*)mats, items, count, m, (double2*)out, item_status,
-            (unsigned long long*)workspace, ws_per_cta / 8, counter);
+        const double2* a0 = (const double2*)mats;
+        double2* o0 = (double2*)out;
+        unsigned long long* w0 = (unsigned long long*)workspace;
+        const size_t wpc = ws_per_cta / 8;
+        if (threads == 256)
+            sz_batched_c128<256><<<grid, 256, smem, st>>>(a0, items, count, m, o0, item_status, w0, wpc, counter);
+        else if (threads == 512)
+            sz_batched_c128<512><<<grid, 512, smem, st>>>(a0, items, count, m, o0, item_status, w0, wpc, counter);
+        else
+            sz_batched_c128<384><<<grid, 384, smem, st>>>(a0, items, count, m, o0, item_status, w0, wpc, counter);
     } else {
         int_batched_fn fn = pick_int_batched(dtype, n_max);
         e = set_smem((const void*)fn, smem);
