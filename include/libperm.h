@@ -154,6 +154,30 @@ perm_status perm_submit(perm_server_t server, const void *host_mat, int n, perm_
 perm_status perm_poll(perm_server_t server, uint64_t ticket, void *out16, int *item_status);
 perm_status perm_server_destroy(perm_server_t server, int timeout_ms);
 
+/* Store-zechin permanent of ONE matrix without allocating any device memory.
+   The paper has no counterpart to this entry point; it exists for callers that
+   cannot call cudaMalloc: code running inside a framework whose pool owns all
+   device memory, loops that cannot afford the device-wide synchronisation an
+   allocation may cause, and threads in the middle of capturing a CUDA graph.
+     mat          device pointer, n*n row-major elements of `dtype`
+     out          device pointer: double2 (PERM_C128) or two uint64 (integers)
+     item_status  device int or NULL (PERM_OK, PERM_EOVERFLOW, PERM_EINVAL)
+   The chain tables live in a fixed 64 MiB scratch array inside the library's
+   device image, held on every device that loads the library until the process
+   exits.  That bounds n: at most 22 for PERM_C128 and 23 for the integer types;
+   larger n (and n < 0, a bad dtype or a NULL pointer) return PERM_EINVAL and
+   launch nothing.  n = 0 gives 1.
+   The first call on a device does a one-time set-up (it looks up the scratch
+   address and uploads a 16 KB index table with cudaMemcpyToSymbol), so make
+   that first call before any stream capture.  The work is asynchronous on
+   `stream`.  Every call shares the one scratch array, which keeps the last
+   call's contents (nothing in it has to start at zero: every table entry is
+   written before it is read); calls whose work overlaps on the GPU, from
+   different streams or threads, race on it and must be serialised by the
+   caller.  Results are identical to perm_batch with PERM_METHOD_SZ. */
+perm_status perm_sz_noalloc(const void *mat, int n, perm_dtype dtype, void *out, int *item_status,
+                            void *stream);
+
 /* Short text for a status code (static storage). */
 const char *perm_strerror(perm_status status);
 

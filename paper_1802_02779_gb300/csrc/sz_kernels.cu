@@ -814,3 +814,90 @@ cudaError_t launch_trivial(int dtype, const ItemDesc* items, int count, void* ou
 }
 
 }  // namespace perm
+
+// ---------------------------------------------------------------------------
+// Allocation-free entry point (perm_sz_noalloc).
+//
+// Some callers cannot call cudaMalloc: a framework that owns every byte of
+// device memory through its own pool, code that must not take the implicit
+// device synchronisation an allocation can cause, or a thread that is in the
+// middle of capturing a CUDA graph.  For them this entry point runs the
+// single-matrix Store-zechin path with its chain tables in a fixed scratch
+// array that lives in the library's device image instead of a plan.
+// ---------------------------------------------------------------------------
+namespace perm {
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = (size_t)64 << 20;     // 64 MiB per device
+constexpr int kNoAllocLow = 13;                               // chain width used by this path
+
+// The scratch itself.  In host code this name is only a stand-in for the
+// symbol; the device address comes from cudaGetSymbolAddress below.
+static __device__ __align__(256) unsigned long long g_noalloc_scratch[kNoAllocScratchBytes / 8];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kNoAllocMaxDevices] = {nullptr};
+unsigned short g_noalloc_hosttab[kMaskTableLen];
+
+__global__ void noalloc_write_one(int dtype, void* out, int* item_status) {
+    if (dtype == PERM_C128) {
+        reinterpret_cast<double2*>(out)[0] = make_double2(1.0, 0.0);
+    } else {
+        reinterpret_cast<unsigned long long*>(out)[0] = 1ull;
+        reinterpret_cast<unsigned long long*>(out)[1] = 0ull;
+    }
+    if (item_status) item_status[0] = PERM_OK;
+}
+
+// Once per device, with that device current: the scratch address and the
+// mask table (filled from a static host array, so nothing is allocated).
+cudaError_t noalloc_setup(int dev, void** scratch) {
+    std::lock_guard<std::mutex> g(g_noalloc_mu);
+    if (g_noalloc_ptr[dev]) { *scratch = g_noalloc_ptr[dev]; return cudaSuccess; }
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    int k = 0;
+    for (int m = 1; m <= kMaxLow; m++)
+        for (int l = 0; l <= m; l++)
+            for (unsigned x = 0; x < (1u << m); x++)
+                if (__builtin_popcount(x) == l) g_noalloc_hosttab[k++] = (unsigned short)x;
+    e = cudaMemcpyToSymbol(g_masks, g_noalloc_hosttab, sizeof(g_noalloc_hosttab));
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = p;
+    *scratch = p;
+    return cudaSuccess;
+}
+
+}  // namespace
+
+// Largest order perm_sz_noalloc accepts for a dtype (its chain tables must fit the scratch).
+int sz_noalloc_max_n(int dtype) {
+    int best = 0;
+    for (int n = 1; n <= kMaxNSZ; n++)
+        if (sz_matrix_workspace_bytes(dtype, n, kNoAllocLow) <= kNoAllocScratchBytes) best = n;
+    return best;
+}
+
+}  // namespace perm
+
+extern "C" perm_status perm_sz_noalloc(const void* mat, int n, perm_dtype dtype, void* out,
+                                       int* item_status, void* stream) {
+    using namespace perm;
+    if (dtype != PERM_C128 && dtype != PERM_U01 && dtype != PERM_I64) return PERM_EINVAL;
+    if (n < 0 || n > sz_noalloc_max_n(dtype) || !out || (n > 0 && !mat)) return PERM_EINVAL;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return PERM_ECUDA;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return PERM_ECUDA;
+    void* scratch = nullptr;
+    if (noalloc_setup(dev, &scratch) != cudaSuccess) return PERM_ECUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n == 0) {
+        noalloc_write_one<<<1, 1, 0, st>>>(dtype, out, item_status);
+        return cudaGetLastError() == cudaSuccess ? PERM_OK : PERM_ECUDA;
+    }
+    const cudaError_t e = sz_launch_single(dtype, mat, 0, n, kNoAllocLow, 0, out, item_status,
+                                           scratch, sms, st);
+    return e == cudaSuccess ? PERM_OK : PERM_ECUDA;
+}

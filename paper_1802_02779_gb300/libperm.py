@@ -58,6 +58,7 @@ _SIGS = {
     "perm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "perm_version": (ctypes.c_char_p, []),
     "perm_measure_fp64_peak": (ctypes.c_int, [ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
+    "perm_sz_noalloc": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP, _VP, _VP]),
 }
 
 _lib = None
