@@ -134,8 +134,8 @@ struct MatCtx {
     const unsigned* rowmask;     // smem: per row, the low columns with a nonzero entry
 };
 
-// Predecessor info for chain H: for the p-th high element h_p (ascending),
-// the slot of H \ h_p among the (s-1)-subsets and the matrix column m + h_p.
+// Predecessor info for chain H: for the p-th outer element h_p (ascending),
+// the slot of H \ h_p among the (s-1)-subsets and its matrix column h_p.
 __device__ __forceinline__ void chain_setup(const MatCtx& mc, unsigned Hmask, int* hinfo) {
     if (threadIdx.x == 0) {
         int hs[kBinomDim];
@@ -150,7 +150,7 @@ __device__ __forceinline__ void chain_setup(const MatCtx& mc, unsigned Hmask, in
                 else if (q > p) slot += bn[hs[q] * (kBinomDim + 1) + q];
             }
             hinfo[p] = (int)slot;
-            hinfo[kBinomDim + p] = mc.m + hs[p];
+            hinfo[kBinomDim + p] = hs[p];          // outer column h is matrix column h
         }
     }
 }
@@ -158,12 +158,20 @@ __device__ __forceinline__ void chain_setup(const MatCtx& mc, unsigned Hmask, in
 // ---------------------------------------------------------------------------
 // complex128 chain.  gprev: previous layer region (chains of 3*CL doubles:
 // uv plane then w plane); gdst: this chain's slot or null.
+//
+// Two phases.  Phase 1 (outer terms): for every entry (H, L) with 2 <= k < n
+// the sum over h in H of a[k-1][h] * T[(H \ h, L)] is streamed from the
+// predecessor chains in global memory -- no dependence inside the chain, so
+// every load of the chain can be in flight at once -- and parked in the
+// entry's shared-memory slot.  Phase 2 (chain terms): sub-level by sub-level,
+// each entry continues its accumulators with the terms of its chain columns,
+// read from shared memory.  Outer columns are 0..t-1 and chain columns t..n-1,
+// so the accumulation order is all columns ascending.
 // ---------------------------------------------------------------------------
-template <bool PIPE>
 __device__ void chain_c128(const MatCtx& mc, int s, unsigned char* chain_smem, const double* gprev,
                            double* gdst, const unsigned char* coef_smem, bool last, double2* out,
                            int out_index) {
-    const int n = mc.n, m = mc.m;
+    const int n = mc.n, m = mc.m, t = mc.t;
     const unsigned CL = mc.chain_len;
     double2* suv = reinterpret_cast<double2*>(chain_smem);
     double* sw = reinterpret_cast<double*>(chain_smem + 16 * CL);
@@ -174,13 +182,51 @@ __device__ void chain_c128(const MatCtx& mc, int s, unsigned char* chain_smem, c
     const int* hcol = mc.hinfo + kBinomDim;
     const unsigned short* masks = mc.masks;
 
+    // ---- phase 1: outer terms ----
+    if (s >= 1) {
+        for (unsigned idx = threadIdx.x; idx < CL; idx += blockDim.x) {
+            const unsigned mask = masks[idx];
+            const int k = s + __popc(mask);
+            if (k < 2 || k >= n) continue;
+            const double2* rxy = cxy + (k - 1) * n;
+            const double* rs = cs + (k - 1) * n;
+            double P1 = 0.0, P2 = 0.0, P3 = 0.0;
+            for (int q = 0; q < s; q += 4) {
+                double2 huv[4];
+                double hw[4];
+#pragma unroll
+                for (int z = 0; z < 4; z++) {
+                    if (q + z < s) {
+                        const double* pc = gprev + (size_t)hslot[q + z] * 3 * CL;
+                        huv[z] = __ldg(reinterpret_cast<const double2*>(pc) + idx);
+                        hw[z] = __ldg(pc + 2 * CL + idx);
+                    }
+                }
+#pragma unroll
+                for (int z = 0; z < 4; z++) {
+                    if (q + z < s) {
+                        const int col = hcol[q + z];
+                        const double2 c = rxy[col];
+                        P1 = __fma_rn(c.x, huv[z].x, P1);
+                        P2 = __fma_rn(c.y, huv[z].y, P2);
+                        P3 = __fma_rn(rs[col], hw[z], P3);
+                    }
+                }
+            }
+            suv[mask] = make_double2(P1, P2);
+            sw[mask] = P3;
+        }
+        __syncthreads();
+    }
+
+    // ---- phase 2: chain terms, sub-level by sub-level ----
     unsigned off = 0;
     for (int l = 0; l <= m; l++) {
         const unsigned cnt = bn[m * (kBinomDim + 1) + l];
         const int k = s + l;
         const int row = k >= 1 ? k - 1 : 0;
-        const double2* rxy = cxy + row * n;
-        const double* rs = cs + row * n;
+        const double2* rxy = cxy + row * n + t;      // chain column j is matrix column t + j
+        const double* rs = cs + row * n + t;
         for (unsigned r = threadIdx.x; r < cnt; r += blockDim.x) {
             const unsigned idx = off + r;
             const unsigned mask = masks[idx];
@@ -188,11 +234,20 @@ __device__ void chain_c128(const MatCtx& mc, int s, unsigned char* chain_smem, c
             if (k == 0) {
                 u = 1.0; v = 0.0; w = 1.0;
             } else if (k == 1) {
-                const int col = (l == 1) ? __ffs(mask) - 1 : hcol[0];
+                const int col = (l == 1) ? t + __ffs(mask) - 1 : hcol[0];
                 u = cxy[col].x; v = cxy[col].y; w = cs[col];
             } else if (k == n) {
-                // the permanent: double-double, four-product complex form
+                // the permanent: double-double, four-product complex form, outer terms first
+                const double2* fxy = cxy + (n - 1) * n;
                 dd2 re = {0.0, 0.0}, im = {0.0, 0.0};
+                for (int q = 0; q < s; q++) {
+                    const double2 p = reinterpret_cast<const double2*>(gprev + (size_t)hslot[q] * 3 * CL)[idx];
+                    const double2 c = fxy[hcol[q]];
+                    re = dd_add_prod(re, c.x, p.x);
+                    re = dd_add_prod(re, -c.y, p.y);
+                    im = dd_add_prod(im, c.x, p.y);
+                    im = dd_add_prod(im, c.y, p.x);
+                }
                 unsigned mm = mask;
                 while (mm) {
                     const int j = __ffs(mm) - 1;
@@ -204,28 +259,13 @@ __device__ void chain_c128(const MatCtx& mc, int s, unsigned char* chain_smem, c
                     im = dd_add_prod(im, c.x, p.y);
                     im = dd_add_prod(im, c.y, p.x);
                 }
-                for (int q = 0; q < s; q++) {
-                    const double2 p = reinterpret_cast<const double2*>(gprev + (size_t)hslot[q] * 3 * CL)[idx];
-                    const double2 c = rxy[hcol[q]];
-                    re = dd_add_prod(re, c.x, p.x);
-                    re = dd_add_prod(re, -c.y, p.y);
-                    im = dd_add_prod(im, c.x, p.y);
-                    im = dd_add_prod(im, c.y, p.x);
-                }
                 u = dd_round(re); v = dd_round(im); w = __dadd_rn(u, v);
             } else {
-                // prefetch up to four high parents before the shared-memory terms
-                double2 huv[4];
-                double hw[4];
-#pragma unroll
-                for (int z = 0; z < 4; z++) {
-                    if (z < s) {
-                        const double* pc = gprev + (size_t)hslot[z] * 3 * CL;
-                        huv[z] = __ldg(reinterpret_cast<const double2*>(pc) + idx);
-                        hw[z] = __ldg(pc + 2 * CL + idx);
-                    }
-                }
                 double P1 = 0.0, P2 = 0.0, P3 = 0.0;
+                if (s >= 1) {                 // outer terms from phase 1
+                    const double2 p = suv[mask];
+                    P1 = p.x; P2 = p.y; P3 = sw[mask];
+                }
                 unsigned mm = mask;
                 while (mm) {
                     const int j = __ffs(mm) - 1;
@@ -237,45 +277,6 @@ __device__ void chain_c128(const MatCtx& mc, int s, unsigned char* chain_smem, c
                     P1 = __fma_rn(c.x, p.x, P1);
                     P2 = __fma_rn(c.y, p.y, P2);
                     P3 = __fma_rn(rs[j], pw, P3);
-                }
-                // high terms in groups of four; with PIPE the next group's loads are
-                // issued before the current group's FMAs (long chains of high terms)
-                for (int q = 0; q < s; q += 4) {
-                    double2 nuv[4];
-                    double nw[4];
-                    if (PIPE) {
-#pragma unroll
-                        for (int z = 0; z < 4; z++) {
-                            if (q + 4 + z < s) {
-                                const double* pc = gprev + (size_t)hslot[q + 4 + z] * 3 * CL;
-                                nuv[z] = __ldg(reinterpret_cast<const double2*>(pc) + idx);
-                                nw[z] = __ldg(pc + 2 * CL + idx);
-                            }
-                        }
-                    } else if (q > 0) {
-#pragma unroll
-                        for (int z = 0; z < 4; z++) {
-                            if (q + z < s) {
-                                const double* pc = gprev + (size_t)hslot[q + z] * 3 * CL;
-                                huv[z] = __ldg(reinterpret_cast<const double2*>(pc) + idx);
-                                hw[z] = __ldg(pc + 2 * CL + idx);
-                            }
-                        }
-                    }
-#pragma unroll
-                    for (int z = 0; z < 4; z++) {
-                        if (q + z < s) {
-                            const int col = hcol[q + z];
-                            const double2 c = rxy[col];
-                            P1 = __fma_rn(c.x, huv[z].x, P1);
-                            P2 = __fma_rn(c.y, huv[z].y, P2);
-                            P3 = __fma_rn(rs[col], hw[z], P3);
-                        }
-                    }
-                    if (PIPE) {
-#pragma unroll
-                        for (int z = 0; z < 4; z++) { huv[z] = nuv[z]; hw[z] = nw[z]; }
-                    }
                 }
                 // Re = P1 - P2, Im = (P3 - P1) - P2, w = Re + Im, each a single
                 // rounding; written as FMAs with +-1 (same results, faster pipe issue)
@@ -297,16 +298,16 @@ __device__ void chain_c128(const MatCtx& mc, int s, unsigned char* chain_smem, c
 }
 
 // ---------------------------------------------------------------------------
-// integer chain modulo 2^64 (W128 = false) or 2^128 (W128 = true).
-// ZO: coefficients are 0/1 (add instead of multiply-add).
-// Global chain: CL words (u64) or CL ulonglong2 (u128).
+// integer chain modulo 2^64 (W128 = false) or 2^128 (W128 = true), same two
+// phases.  ZO: coefficients are 0/1 (add instead of multiply-add).  Global
+// chain: CL words (u64) or CL ulonglong2 (u128).
 // ---------------------------------------------------------------------------
 template <bool W128, bool ZO>
 __device__ void chain_int(const MatCtx& mc, int s, unsigned char* chain_smem,
                           const unsigned long long* gprev, unsigned long long* gdst,
                           const unsigned long long* coef, bool last, unsigned long long* out,
                           int out_index) {
-    const int n = mc.n, m = mc.m;
+    const int n = mc.n, m = mc.m, t = mc.t;
     const unsigned CL = mc.chain_len;
     const unsigned* bn = mc.bn;
     const int* hslot = mc.hinfo;
@@ -316,28 +317,22 @@ __device__ void chain_int(const MatCtx& mc, int s, unsigned char* chain_smem,
     unsigned long long* sv = reinterpret_cast<unsigned long long*>(chain_smem);
     ulonglong2* sv2 = reinterpret_cast<ulonglong2*>(chain_smem);
 
-    unsigned off = 0;
-    for (int l = 0; l <= m; l++) {
-        const unsigned cnt = bn[m * (kBinomDim + 1) + l];
-        const int k = s + l;
-        const unsigned long long* rc = coef + (k >= 1 ? (k - 1) * n : 0);
-        for (unsigned r = threadIdx.x; r < cnt; r += blockDim.x) {
-            const unsigned idx = off + r;
+    // ---- phase 1: outer terms (zero coefficients skipped; a uniform test) ----
+    if (s >= 1) {
+        for (unsigned idx = threadIdx.x; idx < CL; idx += blockDim.x) {
             const unsigned mask = masks[idx];
+            const int k = s + __popc(mask);
+            if (k < 2) continue;
+            const unsigned long long* rc = coef + (k - 1) * n;
             u128 val = {0ull, 0ull};
-            if (k == 0) {
-                val.lo = 1ull;
-            } else if (k == 1) {
-                const int col = (l == 1) ? __ffs(mask) - 1 : hcol[0];
-                val.lo = coef[col];
-            } else {
-                // high parents whose coefficient is nonzero (a uniform test), prefetched
-                unsigned long long hlo[4], hhi[4];
+            for (int q = 0; q < s; q += 4) {
+                unsigned long long hlo[4], hhi[4], hc[4];
 #pragma unroll
                 for (int z = 0; z < 4; z++) {
                     hlo[z] = 0ull; hhi[z] = 0ull;
-                    if (z < s && rc[hcol[z]] != 0ull) {
-                        const unsigned long long* pc = gprev + (size_t)hslot[z] * kW * CL;
+                    hc[z] = (q + z < s) ? rc[hcol[q + z]] : 0ull;
+                    if (hc[z] != 0ull) {
+                        const unsigned long long* pc = gprev + (size_t)hslot[q + z] * kW * CL;
                         if (W128) {
                             const ulonglong2 p = __ldg(reinterpret_cast<const ulonglong2*>(pc) + idx);
                             hlo[z] = p.x; hhi[z] = p.y;
@@ -346,8 +341,43 @@ __device__ void chain_int(const MatCtx& mc, int s, unsigned char* chain_smem,
                         }
                     }
                 }
-                // low terms: only the columns of L whose coefficient is nonzero
-                unsigned mm = mask & mc.rowmask[k - 1];
+#pragma unroll
+                for (int z = 0; z < 4; z++) {
+                    if (hc[z] != 0ull) {
+                        if (W128) val = ZO ? u128_add2(val, hlo[z], hhi[z]) : u128_mac(val, hc[z], hlo[z], hhi[z]);
+                        else val.lo += ZO ? hlo[z] : hc[z] * hlo[z];
+                    }
+                }
+            }
+            if (W128) sv2[mask] = make_ulonglong2(val.lo, val.hi);
+            else sv[mask] = val.lo;
+        }
+        __syncthreads();
+    }
+
+    // ---- phase 2: chain terms ----
+    unsigned off = 0;
+    for (int l = 0; l <= m; l++) {
+        const unsigned cnt = bn[m * (kBinomDim + 1) + l];
+        const int k = s + l;
+        const unsigned long long* rc = coef + (k >= 1 ? (k - 1) * n : 0) + t;
+        const unsigned rmask = k >= 1 ? mc.rowmask[k - 1] : 0u;
+        for (unsigned r = threadIdx.x; r < cnt; r += blockDim.x) {
+            const unsigned idx = off + r;
+            const unsigned mask = masks[idx];
+            u128 val = {0ull, 0ull};
+            if (k == 0) {
+                val.lo = 1ull;
+            } else if (k == 1) {
+                const int col = (l == 1) ? t + __ffs(mask) - 1 : hcol[0];
+                val.lo = coef[col];
+            } else {
+                if (s >= 1) {                 // outer terms from phase 1
+                    if (W128) { const ulonglong2 p = sv2[mask]; val.lo = p.x; val.hi = p.y; }
+                    else val.lo = sv[mask];
+                }
+                // chain terms: only the columns of L whose coefficient is nonzero
+                unsigned mm = mask & rmask;
                 while (mm) {
                     const int j = __ffs(mm) - 1;
                     mm &= mm - 1;
@@ -357,33 +387,6 @@ __device__ void chain_int(const MatCtx& mc, int s, unsigned char* chain_smem,
                         val = ZO ? u128_add2(val, p.x, p.y) : u128_mac(val, rc[j], p.x, p.y);
                     } else {
                         val.lo += ZO ? sv[pm] : rc[j] * sv[pm];
-                    }
-                }
-                for (int q = 0; q < s; q += 4) {
-                    if (q > 0) {
-#pragma unroll
-                        for (int z = 0; z < 4; z++) {
-                            hlo[z] = 0ull; hhi[z] = 0ull;
-                            if (q + z < s && rc[hcol[q + z]] != 0ull) {
-                                const unsigned long long* pc = gprev + (size_t)hslot[q + z] * kW * CL;
-                                if (W128) {
-                                    const ulonglong2 p = __ldg(reinterpret_cast<const ulonglong2*>(pc) + idx);
-                                    hlo[z] = p.x; hhi[z] = p.y;
-                                } else {
-                                    hlo[z] = __ldg(pc + idx);
-                                }
-                            }
-                        }
-                    }
-#pragma unroll
-                    for (int z = 0; z < 4; z++) {
-                        if (q + z < s) {
-                            const unsigned long long c = rc[hcol[q + z]];
-                            if (c) {
-                                if (W128) val = ZO ? u128_add2(val, hlo[z], hhi[z]) : u128_mac(val, c, hlo[z], hhi[z]);
-                                else val.lo += ZO ? hlo[z] : c * hlo[z];
-                            }
-                        }
                     }
                 }
             }
@@ -437,10 +440,11 @@ __device__ inline void load_coef_c128(const double2* a, int n, unsigned char* co
 __device__ inline void load_coef_int(const long long* a, int n, int m, unsigned long long* coef,
                                      unsigned* rowmask) {
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) coef[e] = (unsigned long long)a[e];
+    const int t = n - m;                       // chain column j is matrix column t + j
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         unsigned rm = 0;
         for (int j = 0; j < m; j++)
-            if (a[(size_t)i * n + j] != 0) rm |= 1u << j;
+            if (a[(size_t)i * n + t + j] != 0) rm |= 1u << j;
         rowmask[i] = rm;
     }
 }
@@ -463,13 +467,13 @@ __host__ __device__ inline size_t chain_words(int kind, int m) {
 }
 
 // One chain of a matrix, any element kind.
-template <int KIND, bool ZO, bool PIPE = false>
+template <int KIND, bool ZO>
 __device__ __forceinline__ void run_chain(const MatCtx& mc, int s, unsigned char* smem_chain,
                                           const unsigned long long* src, unsigned long long* dst,
                                           const unsigned char* coef, bool last, void* out,
                                           int out_index) {
     if (KIND == kC128)
-        chain_c128<PIPE>(mc, s, smem_chain, reinterpret_cast<const double*>(src),
+        chain_c128(mc, s, smem_chain, reinterpret_cast<const double*>(src),
                    reinterpret_cast<double*>(dst), coef, last, reinterpret_cast<double2*>(out),
                    out_index);
     else
@@ -592,9 +596,9 @@ sz_layer_c128(const double2* __restrict__ a, int n, int m_param, int s, double2*
     for (unsigned slot = blockIdx.x; slot < nslots; slot += gridDim.x) {
         chain_setup(mc, unrank_high(slot, s, mc.t, mc.bn), reinterpret_cast<int*>(smem + L.hinfo_off));
         __syncthreads();
-        run_chain<kC128, false, true>(mc, s, smem + L.chain_off, src_region,
-                                      last ? nullptr : dst_region + (size_t)slot * CW, smem + L.coef_off,
-                                      last, out, out_index);
+        run_chain<kC128, false>(mc, s, smem + L.chain_off, src_region,
+                                last ? nullptr : dst_region + (size_t)slot * CW, smem + L.coef_off,
+                                last, out, out_index);
     }
     if (last && blockIdx.x == 0 && threadIdx.x == 0 && item_status) item_status[out_index] = PERM_OK;
 }
