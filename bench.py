@@ -371,7 +371,87 @@ def measure_extras(lp, torch, cm, im, stream, c_kernel_ms, count):
             res[name + "_value"] = [float(o32[0].real), float(o32[0].imag)]
     res["sz_fp64_tflops"] = sz_c128_flops(32) / (res["store_zechin_ms"] / 1000.0) / 1e12
     out["n32"] = res
+    out["uneven"] = measure_uneven(lp, torch, stream)
+    out["serving"] = measure_serving(lp)
     return out
+
+
+def measure_uneven(lp, torch, stream, count=1000):
+    """Uneven-size batching: a prefix of the 20000-request stream (n uniform in 8..28,
+    70% complex Haar submatrices, 30% 0/1 at density 0.3-0.7), plain per-matrix
+    launches vs one batched call per dtype vs the same call replayed as a CUDA graph."""
+    from paper_1802_02779_gb300 import workloads as wl
+    reqs = wl.uneven_requests(count=count)
+    groups = {}
+    for dt in ("c128", "u01"):
+        mats = [r.mat for r in reqs if r.dtype == dt]
+        sizes = [m.shape[0] for m in mats]
+        npdt = np.complex128 if dt == "c128" else np.int64
+        flat = np.concatenate([np.ascontiguousarray(m, dtype=npdt).reshape(-1) for m in mats])
+        dev = torch.from_numpy(flat).cuda()
+        out = torch.empty((len(mats), 2), dtype=torch.float64 if dt == "c128" else torch.int64, device="cuda")
+        groups[dt] = (sizes, dev, out)
+    side = torch.cuda.Stream()
+    res = {"requests": count, "n_range": [8, 28]}
+    for name, flags in (("plain", lp.FLAG_PLAIN), ("batched", 0), ("graph", lp.FLAG_GRAPH)):
+        plans = {dt: lp.Plan(28, dt, flags=flags, max_batch=count) for dt in groups}
+        times = []
+        for rep in range(2):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            with torch.cuda.stream(side):
+                for dt, (sizes, dev, out) in groups.items():
+                    plans[dt].batch(dev, sizes, out, None, side)
+            side.synchronize()
+            times.append(time.perf_counter() - t0)
+        for p in plans.values():
+            p.close()
+        res[name + "_perm_per_s"] = count / times[-1]
+    res["batched_vs_plain"] = res["batched_perm_per_s"] / res["plain_perm_per_s"]
+    res["graph_vs_plain"] = res["graph_perm_per_s"] / res["plain_perm_per_s"]
+    return res
+
+
+def measure_serving(lp, arrival_window_s=20.0, drain_s=120.0, calib=12):
+    """Serving loop under Poisson arrivals: n uniform in 10..36, 70% complex
+    Haar submatrices, 30% 0/1.  The arrival rate is 0.8 x the capacity measured
+    by serving `calib` requests of the same distribution back to back.  Latency =
+    completion seen by perm_poll minus the scheduled arrival."""
+    from paper_1802_02779_gb300 import workloads as wl
+    pool = wl.uneven_requests(count=400, seed=wl.SEED_BASE + 8, n_lo=10, n_hi=36)
+    with lp.Server() as srv:
+        t0 = time.perf_counter()
+        tk = [srv.submit(r.mat, r.dtype) for r in pool[:calib]]
+        srv.wait_all(tk, timeout_s=600)
+        capacity = calib / (time.perf_counter() - t0)
+        rate = 0.8 * capacity
+        g = np.random.default_rng(wl.SEED_BASE + 8)
+        arrivals = np.cumsum(g.exponential(1.0 / rate, size=len(pool)))
+        arrivals = arrivals[arrivals < arrival_window_s]
+        reqs = pool[calib:calib + len(arrivals)]
+        pending = {}
+        lat = []
+        start = time.perf_counter()
+        i = 0
+        while i < len(reqs) or pending:
+            now = time.perf_counter() - start
+            while i < len(reqs) and arrivals[i] <= now:
+                pending[srv.submit(reqs[i].mat, reqs[i].dtype)] = arrivals[i]
+                i += 1
+            for t in list(pending):
+                state, _ = srv.poll(t)
+                if state == "done":
+                    lat.append(time.perf_counter() - start - pending.pop(t))
+            if now > arrival_window_s + drain_s:
+                break
+            time.sleep(0.0005)
+        elapsed = time.perf_counter() - start
+    lat = np.array(lat)
+    return {"arrival_rate_per_s": rate, "capacity_per_s": capacity, "requests": int(len(reqs)),
+            "completed": int(len(lat)), "p50_ms": float(np.percentile(lat, 50) * 1e3) if len(lat) else None,
+            "p99_ms": float(np.percentile(lat, 99) * 1e3) if len(lat) else None,
+            "perm_per_s": float(len(lat) / elapsed), "n_range": [10, 36],
+            "table_budget": "server default (min(80 GB, free/3))"}
 
 
 def run_single(args):

@@ -43,7 +43,8 @@
  * Ownership: the caller owns every input and output buffer; the library owns
  * its workspace (Store-zechin tables, Ryser partial sums, item descriptors),
  * allocated in perm_plan_create and freed in perm_plan_destroy.  perm_batch
- * itself never allocates.
+ * itself never allocates, except for the one-time graph set-up of
+ * PERM_FLAG_GRAPH.
  *
  * Errors: argument errors are returned synchronously and nothing is launched.
  * CUDA failures map to PERM_ECUDA.  Per-matrix conditions go to item_status.
@@ -88,6 +89,12 @@ typedef enum perm_method {
 
 /* perm_opts.flags */
 #define PERM_FLAG_PLAIN 1u    /* one kernel launch per matrix (the unbatched baseline) */
+#define PERM_FLAG_GRAPH 2u    /* capture each batch shape as a CUDA graph and replay it: the
+                                 first perm_batch call with a given (sizes, mats, out,
+                                 item_status) on a non-default stream allocates a small
+                                 descriptor buffer, captures and instantiates a graph; later
+                                 calls with the same signature only launch the graph (16 are
+                                 cached per plan, least recently used evicted) */
 
 typedef struct perm_opts {
     size_t mem_budget_bytes;  /* workspace cap; 0 = 45% of the free device memory */

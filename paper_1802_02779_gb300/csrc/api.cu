@@ -23,6 +23,28 @@
 
 using namespace perm;
 
+constexpr size_t kGraphCacheCap = 16;
+
+// One captured batch (PERM_FLAG_GRAPH): its launch sequence as a CUDA graph.
+struct GraphEntry {
+    unsigned long long key = 0;
+    int count = 0;
+    std::vector<int> sizes;
+    const void* mats = nullptr;
+    const void* out = nullptr;
+    const int* status = nullptr;
+    ItemDesc* desc = nullptr;          // device copy of the descriptors the graph reads
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    unsigned long long last_use = 0;
+    void release() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (desc) cudaFree(desc);
+        exec = nullptr; graph = nullptr; desc = nullptr;
+    }
+};
+
 struct perm_plan_s {
     int device = 0;
     int n_max = 0;
@@ -63,6 +85,10 @@ struct perm_plan_s {
     size_t d_in_bytes = 0;
     void* d_out = nullptr;
     int* d_status = nullptr;
+
+    // graph cache (PERM_FLAG_GRAPH)
+    std::vector<GraphEntry> graphs;
+    unsigned long long graph_clock = 0;
 };
 
 namespace {
@@ -221,6 +247,8 @@ extern "C" {
 perm_status perm_plan_destroy(perm_plan_t p) {
     if (!p) return PERM_OK;
     cudaDeviceSynchronize();
+    for (auto& g : p->graphs) g.release();
+    p->graphs.clear();
     if (p->ext_ws) p->ws = nullptr;
     release(p->ws);
     release(p->partials);
@@ -239,22 +267,24 @@ size_t perm_plan_workspace_bytes(perm_plan_t p) {
     return p ? p->ws_bytes + p->partials_bytes + p->stage_bytes + p->d_in_bytes : 0;
 }
 
-perm_status perm_batch(perm_plan_t p, const void* mats, const int* sizes, int count, void* out,
-                       int* item_status, void* stream) {
-    if (!p || count < 0) return PERM_EINVAL;
-    if (count == 0) return PERM_OK;
-    if (!sizes || !out || count > p->max_batch) return PERM_EINVAL;
-    cudaStream_t st = (cudaStream_t)stream;
-    bool any_nonempty = false;
-    for (int i = 0; i < count; i++) {
-        if (sizes[i] < 0 || sizes[i] > p->n_max) return PERM_EINVAL;
-        if (sizes[i] > 0) any_nonempty = true;
-    }
-    if (any_nonempty && !mats) return PERM_EINVAL;
+}  // extern "C"
 
-    // ---- classify ----
+namespace {
+
+// Classification of one batch: descriptors in launch order and the launch list.
+struct BatchLayout {
+    std::vector<ItemDesc> desc;      // [n = 0 items][batched Store-zechin][Ryser groups by n]
+    size_t triv_at = 0, ntriv = 0;
+    size_t szb_at = 0, nszb = 0;
+    int szb_nmax = 0;
+    std::vector<ItemDesc> szs;       // one-at-a-time Store-zechin (descriptors passed by value)
+    struct Group { int n; size_t at; int cnt; };
+    std::vector<Group> ry;
+};
+
+perm_status classify(perm_plan_t p, const int* sizes, int count, BatchLayout& L) {
     const bool plain = (p->flags & PERM_FLAG_PLAIN) != 0;
-    std::vector<ItemDesc> triv, szb, szs;
+    std::vector<ItemDesc> triv, szb;
     std::map<int, std::vector<ItemDesc>> ry;   // by n, ascending
     long long off = 0;
     for (int i = 0; i < count; i++) {
@@ -271,74 +301,160 @@ perm_status perm_batch(perm_plan_t p, const void* mats, const int* sizes, int co
         }
         if (use_sz) {
             if (!plain && n <= p->sz_batch_nmax) szb.push_back(d);
-            else szs.push_back(d);
+            else L.szs.push_back(d);
         } else {
             ry[n].push_back(d);
         }
     }
     // longest matrices first for the persistent queue
     std::stable_sort(szb.begin(), szb.end(), [](const ItemDesc& a, const ItemDesc& b) { return a.n > b.n; });
-
-    // ---- stage descriptors: [triv][szb][ry items by n] ----
-    size_t n_items = triv.size() + szb.size();
-    for (auto& kv : ry) n_items += kv.second.size();
-    const size_t used = n_items * sizeof(ItemDesc);
-    if (used > p->stage_bytes) return PERM_EINVAL;
-    cudaError_t e = cudaEventSynchronize(p->stage_free);   // previous upload finished reading
-    if (e != cudaSuccess) return PERM_ECUDA;
-    ItemDesc* hd = reinterpret_cast<ItemDesc*>(p->h_stage);
-    size_t k = 0;
-    const size_t triv_at = k;
-    for (auto& d : triv) hd[k++] = d;
-    const size_t szb_at = k;
-    for (auto& d : szb) hd[k++] = d;
-    std::vector<size_t> ry_at;
+    L.triv_at = L.desc.size();
+    L.ntriv = triv.size();
+    L.desc.insert(L.desc.end(), triv.begin(), triv.end());
+    L.szb_at = L.desc.size();
+    L.nszb = szb.size();
+    L.szb_nmax = szb.empty() ? 0 : szb.front().n;
+    L.desc.insert(L.desc.end(), szb.begin(), szb.end());
     for (auto& kv : ry) {
-        ry_at.push_back(k);
-        for (auto& d : kv.second) hd[k++] = d;
+        L.ry.push_back({kv.first, L.desc.size(), (int)kv.second.size()});
+        L.desc.insert(L.desc.end(), kv.second.begin(), kv.second.end());
     }
-    e = cudaMemcpyAsync(p->d_stage, p->h_stage, used, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaEventRecord(p->stage_free, st);
-    if (e != cudaSuccess) return PERM_ECUDA;
-    const ItemDesc* dd = reinterpret_cast<const ItemDesc*>(p->d_stage);
+    return PERM_OK;
+}
 
-    // ---- launches ----
-    if (!triv.empty()) {
-        e = launch_trivial(p->dtype, dd + triv_at, (int)triv.size(), out, item_status, st);
+// Enqueue every launch of a classified batch on `st` (descriptors at `dd` on the device).
+perm_status enqueue(perm_plan_t p, const BatchLayout& L, const void* mats, const ItemDesc* dd,
+                    void* out, int* item_status, cudaStream_t st) {
+    const bool plain = (p->flags & PERM_FLAG_PLAIN) != 0;
+    cudaError_t e;
+    if (L.ntriv) {
+        e = launch_trivial(p->dtype, dd + L.triv_at, (int)L.ntriv, out, item_status, st);
         if (e != cudaSuccess) return PERM_ECUDA;
     }
-    if (!szb.empty()) {
+    if (L.nszb) {
         e = cudaMemsetAsync(p->d_counter, 0, sizeof(unsigned), st);
         if (e != cudaSuccess) return PERM_ECUDA;
-        const int grid = std::min<int>(p->sz_grid, (int)szb.size());
-        e = sz_launch_batched(p->dtype, mats, dd + szb_at, (int)szb.size(), szb.front().n, p->m_low,
+        const int grid = std::min<int>(p->sz_grid, (int)L.nszb);
+        e = sz_launch_batched(p->dtype, mats, dd + L.szb_at, (int)L.nszb, L.szb_nmax, p->m_low,
                               p->c128_threads, out, item_status, p->ws, p->sz_ws_per_cta, grid,
                               p->d_counter, st);
         if (e != cudaSuccess) return PERM_ECUDA;
     }
-    for (auto& d : szs) {
+    for (auto& d : L.szs) {
         e = sz_launch_single(p->dtype, mats, d.offset, d.n, p->m_single, d.out_index, out, item_status,
                              p->ws, p->num_sms, st);
         if (e != cudaSuccess) return PERM_ECUDA;
     }
-    size_t g = 0;
-    for (auto& kv : ry) {
-        const int n = kv.first;
-        const int cnt = (int)kv.second.size();
-        const long long parts = ryser_parts(p->dtype, n);
-        const ItemDesc* items = dd + ry_at[g];
+    for (auto& g : L.ry) {
+        const long long parts = ryser_parts(p->dtype, g.n);
         // matrices per launch limited by the partials buffer (and one per launch when plain)
         long long per_launch = std::max<long long>(1, p->partials_cap / parts);
         if (plain) per_launch = 1;
-        for (int b0 = 0; b0 < cnt; b0 += (int)per_launch) {
-            const int c = (int)std::min<long long>(per_launch, cnt - b0);
-            e = ryser_launch_group(p->dtype, n, mats, items + b0, c, p->partials, out, item_status,
-                                   p->num_sms * 8, st);
+        for (int b0 = 0; b0 < g.cnt; b0 += (int)per_launch) {
+            const int c = (int)std::min<long long>(per_launch, g.cnt - b0);
+            e = ryser_launch_group(p->dtype, g.n, mats, dd + g.at + b0, c, p->partials, out,
+                                   item_status, p->num_sms * 8, st);
             if (e != cudaSuccess) return PERM_ECUDA;
         }
-        g++;
     }
     return PERM_OK;
+}
+
+unsigned long long batch_key(const void* mats, const int* sizes, int count, const void* out,
+                             const int* item_status) {
+    // FNV-1a over the shape and the buffer addresses
+    unsigned long long h = 1469598103934665603ull;
+    auto mix = [&h](unsigned long long v) {
+        for (int b = 0; b < 8; b++) { h ^= (v >> (8 * b)) & 0xff; h *= 1099511628211ull; }
+    };
+    mix((unsigned long long)(uintptr_t)mats);
+    mix((unsigned long long)(uintptr_t)out);
+    mix((unsigned long long)(uintptr_t)item_status);
+    mix((unsigned long long)count);
+    for (int i = 0; i < count; i++) mix((unsigned long long)sizes[i]);
+    return h;
+}
+
+perm_status batch_graph(perm_plan_t p, const void* mats, const int* sizes, int count, void* out,
+                        int* item_status, cudaStream_t st) {
+    const unsigned long long key = batch_key(mats, sizes, count, out, item_status);
+    for (auto& g : p->graphs) {
+        if (g.key == key && g.count == count && g.sizes == std::vector<int>(sizes, sizes + count) &&
+            g.mats == mats && g.out == out && g.status == item_status) {
+            g.last_use = ++p->graph_clock;
+            return cudaGraphLaunch(g.exec, st) == cudaSuccess ? PERM_OK : PERM_ECUDA;
+        }
+    }
+    BatchLayout L;
+    perm_status ps = classify(p, sizes, count, L);
+    if (ps != PERM_OK) return ps;
+    GraphEntry g;
+    g.key = key;
+    g.count = count;
+    g.sizes.assign(sizes, sizes + count);
+    g.mats = mats;
+    g.out = out;
+    g.status = item_status;
+    const size_t bytes = std::max<size_t>(1, L.desc.size()) * sizeof(ItemDesc);
+    if (cudaMalloc(&g.desc, bytes) != cudaSuccess) { cudaGetLastError(); return PERM_ENOMEM; }
+    cudaError_t e = cudaMemcpy(g.desc, L.desc.data(), L.desc.size() * sizeof(ItemDesc), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) { cudaFree(g.desc); return PERM_ECUDA; }
+    ps = enqueue(p, L, mats, g.desc, out, item_status, st);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(st, &graph);
+    if (ps != PERM_OK || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaFree(g.desc);
+        cudaGetLastError();
+        return ps != PERM_OK ? ps : PERM_ECUDA;
+    }
+    g.graph = graph;
+    e = cudaGraphInstantiate(&g.exec, graph, 0);
+    if (e != cudaSuccess) { cudaGraphDestroy(graph); cudaFree(g.desc); return PERM_ECUDA; }
+    if (p->graphs.size() >= kGraphCacheCap) {   // evict the least recently used graph
+        auto it = std::min_element(p->graphs.begin(), p->graphs.end(),
+                                   [](const GraphEntry& a, const GraphEntry& b) { return a.last_use < b.last_use; });
+        cudaStreamSynchronize(st);
+        it->release();
+        p->graphs.erase(it);
+    }
+    g.last_use = ++p->graph_clock;
+    p->graphs.push_back(g);
+    return cudaGraphLaunch(g.exec, st) == cudaSuccess ? PERM_OK : PERM_ECUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+perm_status perm_batch(perm_plan_t p, const void* mats, const int* sizes, int count, void* out,
+                       int* item_status, void* stream) {
+    if (!p || count < 0) return PERM_EINVAL;
+    if (count == 0) return PERM_OK;
+    if (!sizes || !out || count > p->max_batch) return PERM_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    bool any_nonempty = false;
+    for (int i = 0; i < count; i++) {
+        if (sizes[i] < 0 || sizes[i] > p->n_max) return PERM_EINVAL;
+        if (sizes[i] > 0) any_nonempty = true;
+    }
+    if (any_nonempty && !mats) return PERM_EINVAL;
+    if ((p->flags & PERM_FLAG_GRAPH) && st != nullptr)
+        return batch_graph(p, mats, sizes, count, out, item_status, st);
+
+    BatchLayout L;
+    perm_status ps = classify(p, sizes, count, L);
+    if (ps != PERM_OK) return ps;
+    const size_t used = L.desc.size() * sizeof(ItemDesc);
+    if (used > p->stage_bytes) return PERM_EINVAL;
+    cudaError_t e = cudaEventSynchronize(p->stage_free);   // previous upload finished reading
+    if (e != cudaSuccess) return PERM_ECUDA;
+    if (used) std::memcpy(p->h_stage, L.desc.data(), used);
+    if (used) e = cudaMemcpyAsync(p->d_stage, p->h_stage, used, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaEventRecord(p->stage_free, st);
+    if (e != cudaSuccess) return PERM_ECUDA;
+    return enqueue(p, L, mats, reinterpret_cast<const ItemDesc*>(p->d_stage), out, item_status, st);
 }
 
 perm_status perm_batch_host(perm_plan_t p, const void* mats, const int* sizes, int count, void* out,

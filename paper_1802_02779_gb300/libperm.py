@@ -24,6 +24,7 @@ PERM_C128, PERM_U01, PERM_I64 = 1, 2, 3
 # perm_method
 METHOD_AUTO, METHOD_SZ, METHOD_RYSER = 0, 1, 2
 FLAG_PLAIN = 1
+FLAG_GRAPH = 2
 
 DTYPES = {"c128": PERM_C128, "u01": PERM_U01, "i64": PERM_I64}
 

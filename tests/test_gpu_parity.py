@@ -152,3 +152,42 @@ def test_sz_and_ryser_agree_n24(lp):
     b = lp.permanents([m], "c128", method=lp.METHOD_RYSER)[0]
     scale = oracle.per_abs(m)
     assert abs(a - b) <= 2e-12 * scale
+
+
+# ---------------------------------------------------------------------------
+# CUDA-graph replay (PERM_FLAG_GRAPH): same bits as direct launches, and a
+# replay reads the buffers' current contents
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("method", ["auto", "ryser"])
+def test_graph_replay(lp, method):
+    sizes = [0, 6, 12, 20, 23, 14, 20, 9]
+    mats = [rand_complex(n, 8100 + i) for i, n in enumerate(sizes)]
+    flat = np.concatenate([m.reshape(-1) for m in mats])
+    dev = torch.from_numpy(flat).cuda()
+    s = torch.cuda.Stream()
+    outs = {}
+    for flags in (0, lp.FLAG_GRAPH):
+        with lp.Plan(max(sizes), "c128", method=meth(lp, method), flags=flags) as p:
+            out = torch.empty(len(sizes), dtype=torch.complex128, device="cuda")
+            st = torch.empty(len(sizes), dtype=torch.int32, device="cuda")
+            res = []
+            for rep in range(3):
+                with torch.cuda.stream(s):
+                    p.batch(dev, sizes, out, st, s)
+                s.synchronize()
+                res.append(out.cpu().numpy().copy())
+                assert int(st.abs().sum()) == 0
+            assert (res[0] == res[1]).all() and (res[1] == res[2]).all()
+            # new contents, same buffers: scale matrix 3 (n = 20) by 2 -> per times 2^20
+            dev2 = dev.clone()
+            o3 = sum(n * n for n in sizes[:3])
+            dev.view(-1)[o3:o3 + 20 * 20] *= 2
+            with torch.cuda.stream(s):
+                p.batch(dev, sizes, out, st, s)
+            s.synchronize()
+            scaled = out.cpu().numpy().copy()
+            dev.copy_(dev2)
+            outs[flags] = (res[0], scaled)
+    assert (outs[0][0] == outs[lp.FLAG_GRAPH][0]).all()
+    assert (outs[0][1] == outs[lp.FLAG_GRAPH][1]).all()
+    assert outs[0][1][3] == outs[0][0][3] * 2 ** 20
