@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--n", type=int, default=32)
     ap.add_argument("--method", default="sz", choices=["sz", "ryser"])
     ap.add_argument("--dtype", default="c128", choices=["c128", "u01"])
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="use the default CTA size and chain width (profiling runs)")
     return ap.parse_args()
 
 
@@ -224,8 +226,9 @@ def run_gpu(args, rank, world):
     i_out = torch.empty((count, 2), dtype=torch.int64, device="cuda")
     c_st = torch.empty(count, dtype=torch.int32, device="cuda")
     i_st = torch.empty(count, dtype=torch.int32, device="cuda")
-    pc = lp.Plan(N, "c128", max_batch=count)
-    pi = lp.Plan(N, "u01", max_batch=count)
+    tune = 0 if args.no_autotune else lp.FLAG_AUTOTUNE
+    pc = lp.Plan(N, "c128", max_batch=count, flags=tune)
+    pi = lp.Plan(N, "u01", max_batch=count, flags=tune)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
@@ -320,6 +323,7 @@ def run_gpu(args, rank, world):
             "config": {"workload": WORKLOAD, "n": N, "complex128": count, "zero_one": count,
                        "method": "Store-zechin, persistent batched launch (one CTA per matrix)",
                        "l2": "flushed between timed steps (256 MB write)",
+                       "plans": {"complex128": pc.describe(), "zero_one": pi.describe()},
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "complex_perm_per_s": count / (c_kernel_ms / 1000.0),
             "zero_one_perm_per_s": count / (float(np.mean(i_ms)) / 1000.0),
@@ -412,23 +416,28 @@ def measure_uneven(lp, torch, stream, count=1000):
     return res
 
 
-def measure_serving(lp, arrival_window_s=20.0, drain_s=120.0, calib=12):
+def measure_serving(lp, arrival_window_s=60.0, drain_s=120.0):
     """Serving loop under Poisson arrivals: n uniform in 10..36, 70% complex
     Haar submatrices, 30% 0/1.  The arrival rate is 0.8 x the capacity measured
-    by serving `calib` requests of the same distribution back to back.  Latency =
-    completion seen by perm_poll minus the scheduled arrival."""
+    by serving one request of every order 10..36 (complex, the costlier kind)
+    back to back.  Latency = completion seen by perm_poll minus the scheduled
+    arrival."""
     from paper_1802_02779_gb300 import workloads as wl
-    pool = wl.uneven_requests(count=400, seed=wl.SEED_BASE + 8, n_lo=10, n_hi=36)
+    pool = wl.uneven_requests(count=2000, seed=wl.SEED_BASE + 8, n_lo=10, n_hi=36)
+    u = wl.haar_unitary(256, wl.SEED_BASE + 7)
+    gcal = np.random.default_rng(wl.SEED_BASE + 9)
+    calib = [np.ascontiguousarray(u[:n][:, np.sort(gcal.choice(256, size=n, replace=False))])
+             for n in range(10, 37)]
     with lp.Server() as srv:
         t0 = time.perf_counter()
-        tk = [srv.submit(r.mat, r.dtype) for r in pool[:calib]]
-        srv.wait_all(tk, timeout_s=600)
-        capacity = calib / (time.perf_counter() - t0)
+        tk = [srv.submit(m, "c128") for m in calib]
+        srv.wait_all(tk, timeout_s=900)
+        capacity = len(calib) / (time.perf_counter() - t0)
         rate = 0.8 * capacity
         g = np.random.default_rng(wl.SEED_BASE + 8)
         arrivals = np.cumsum(g.exponential(1.0 / rate, size=len(pool)))
         arrivals = arrivals[arrivals < arrival_window_s]
-        reqs = pool[calib:calib + len(arrivals)]
+        reqs = pool[:len(arrivals)]
         pending = {}
         lat = []
         start = time.perf_counter()
@@ -451,6 +460,7 @@ def measure_serving(lp, arrival_window_s=20.0, drain_s=120.0, calib=12):
             "completed": int(len(lat)), "p50_ms": float(np.percentile(lat, 50) * 1e3) if len(lat) else None,
             "p99_ms": float(np.percentile(lat, 99) * 1e3) if len(lat) else None,
             "perm_per_s": float(len(lat) / elapsed), "n_range": [10, 36],
+            "calibration": "one complex request of each n = 10..36 served back to back",
             "table_budget": "server default (min(80 GB, free/3))"}
 
 

@@ -95,6 +95,10 @@ typedef enum perm_method {
                                  descriptor buffer, captures and instantiates a graph; later
                                  calls with the same signature only launch the graph (16 are
                                  cached per plan, least recently used evicted) */
+#define PERM_FLAG_AUTOTUNE 4u /* at plan creation, time every CTA size and chain width of the
+                                 batched Store-zechin kernel on a synthetic batch and keep the
+                                 fastest (results are bit-identical for every choice); cached
+                                 per process and in the file LIBPERM_TUNE_CACHE names, if set */
 
 typedef struct perm_opts {
     size_t mem_budget_bytes;  /* workspace cap; 0 = 45% of the free device memory */
@@ -120,6 +124,11 @@ perm_status perm_plan_destroy(perm_plan_t plan);
 
 /* Workspace bytes the plan holds on the device. */
 size_t perm_plan_workspace_bytes(perm_plan_t plan);
+
+/* A JSON description of the plan's choices (methods' order limits, chain widths,
+   CTA size, grid, workspace, whether it was autotuned), written like snprintf
+   into buf[len]; returns the length it needed, or -1 for a NULL plan. */
+int perm_plan_describe(perm_plan_t plan, char *buf, size_t len);
 
 /* Permanents of `count` matrices, asynchronously on `stream` (a cudaStream_t;
    NULL = the legacy default stream).

@@ -18,6 +18,8 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
+#include <tuple>
 #include <new>
 #include <vector>
 
@@ -77,6 +79,7 @@ struct perm_plan_s {
     size_t stage_bytes = 0;
     cudaEvent_t stage_free = nullptr;
     unsigned* d_counter = nullptr;
+    int* d_widths = nullptr;      // integer Ryser: width per matrix of a launch
 
     bool ext_ws = false;          // workspace owned by someone else (the server)
 
@@ -85,6 +88,8 @@ struct perm_plan_s {
     size_t d_in_bytes = 0;
     void* d_out = nullptr;
     int* d_status = nullptr;
+
+    bool tuned = false;           // chosen by the autotuner
 
     // graph cache (PERM_FLAG_GRAPH)
     std::vector<GraphEntry> graphs;
@@ -119,6 +124,10 @@ int sz_batch_limit(perm_plan_t p) {
 // Plan creation with an optional caller-owned Store-zechin workspace.
 perm_status plan_create_impl(int n_max, perm_dtype dtype, const perm_opts* opts, void* ext_ws,
                              size_t ext_ws_bytes, perm_plan_t* out);
+static perm_status plan_create_tuned(int n_max, perm_dtype dtype, const perm_opts* opts,
+                                     perm_plan_t* out);
+static perm_status plan_create_core(int n_max, perm_dtype dtype, const perm_opts* opts, void* ext_ws,
+                                    size_t ext_ws_bytes, int threads, perm_plan_t* out);
 
 extern "C" {
 
@@ -140,6 +149,7 @@ const char* perm_strerror(perm_status s) {
 const char* perm_version(void) { return "0.1.0"; }
 
 perm_status perm_plan_create(int n_max, perm_dtype dtype, const perm_opts* opts, perm_plan_t* out) {
+    if (opts && (opts->flags & PERM_FLAG_AUTOTUNE)) return plan_create_tuned(n_max, dtype, opts, out);
     return plan_create_impl(n_max, dtype, opts, nullptr, 0, out);
 }
 
@@ -147,6 +157,11 @@ perm_status perm_plan_create(int n_max, perm_dtype dtype, const perm_opts* opts,
 
 perm_status plan_create_impl(int n_max, perm_dtype dtype, const perm_opts* opts, void* ext_ws,
                              size_t ext_ws_bytes, perm_plan_t* out) {
+    return plan_create_core(n_max, dtype, opts, ext_ws, ext_ws_bytes, 0, out);
+}
+
+static perm_status plan_create_core(int n_max, perm_dtype dtype, const perm_opts* opts, void* ext_ws,
+                                    size_t ext_ws_bytes, int threads, perm_plan_t* out) {
     if (!out) return PERM_EINVAL;
     *out = nullptr;
     if (n_max < 0 || n_max > kMaxN || !valid_dtype(dtype)) return PERM_EINVAL;
@@ -169,6 +184,12 @@ perm_status plan_create_impl(int n_max, perm_dtype dtype, const perm_opts* opts,
     // experiment knobs (results are bit-identical for every choice)
     if (const char* v = getenv("LIBPERM_SZ_LOW")) { int x = atoi(v); if (x >= 1 && x <= kMaxLow) p->m_low = x; }
     if (const char* v = getenv("LIBPERM_SZ_THREADS")) { int x = atoi(v); if (sz_c128_threads_valid(x)) p->c128_threads = x; }
+    if (threads < 0) {               // tuned: -(m_low * 1000 + threads)
+        const int code = -threads;
+        p->m_low = code / 1000;
+        threads = code % 1000;
+    }
+    if (threads && sz_c128_threads_valid(threads)) p->c128_threads = threads;
     cudaError_t e = cudaGetDevice(&p->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
     size_t free_b = 0, total_b = 0;
@@ -232,6 +253,7 @@ perm_status plan_create_impl(int n_max, perm_dtype dtype, const perm_opts* opts,
     if (e == cudaSuccess) e = cudaMalloc(&p->d_stage, p->stage_bytes);
     if (e == cudaSuccess) e = cudaMallocHost(&p->h_stage, p->stage_bytes);
     if (e == cudaSuccess) e = cudaMalloc(&p->d_counter, 64 * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_widths, (size_t)p->max_batch * sizeof(int));
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->stage_free, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -254,6 +276,7 @@ perm_status perm_plan_destroy(perm_plan_t p) {
     release(p->partials);
     release(p->d_stage);
     release(p->d_counter);
+    release(p->d_widths);
     release(p->d_in);
     release(p->d_out);
     release(p->d_status);
@@ -261,6 +284,19 @@ perm_status perm_plan_destroy(perm_plan_t p) {
     if (p->stage_free) cudaEventDestroy(p->stage_free);
     delete p;
     return PERM_OK;
+}
+
+int perm_plan_describe(perm_plan_t p, char* buf, size_t len) {
+    if (!p) return -1;
+    const char* dt = p->dtype == PERM_C128 ? "c128" : (p->dtype == PERM_U01 ? "u01" : "i64");
+    return snprintf(buf, len,
+                    "{\"dtype\": \"%s\", \"n_max\": %d, \"method\": %d, \"flags\": %u, "
+                    "\"sz_batch_nmax\": %d, \"sz_single_nmax\": %d, \"chain_width_batched\": %d, "
+                    "\"chain_width_single\": %d, \"complex_cta_threads\": %d, \"batched_grid\": %d, "
+                    "\"workspace_bytes\": %zu, \"autotuned\": %s}",
+                    dt, p->n_max, p->method, p->flags, p->sz_batch_nmax, p->sz_single_nmax, p->m_low,
+                    p->m_single, p->c128_threads, p->sz_grid, perm_plan_workspace_bytes(p),
+                    p->tuned ? "true" : "false");
 }
 
 size_t perm_plan_workspace_bytes(perm_plan_t p) {
@@ -341,8 +377,11 @@ perm_status enqueue(perm_plan_t p, const BatchLayout& L, const void* mats, const
         if (e != cudaSuccess) return PERM_ECUDA;
     }
     for (auto& d : L.szs) {
+        // two CTAs' worth of chains per SM and layer: the per-CTA set-up is amortised, and
+        // every layer is its own launch, which gives the scheduler a point to interleave
+        // work from higher-priority streams
         e = sz_launch_single(p->dtype, mats, d.offset, d.n, p->m_single, d.out_index, out, item_status,
-                             p->ws, p->num_sms, st);
+                             p->ws, 2 * p->num_sms, st);
         if (e != cudaSuccess) return PERM_ECUDA;
     }
     for (auto& g : L.ry) {
@@ -352,8 +391,8 @@ perm_status enqueue(perm_plan_t p, const BatchLayout& L, const void* mats, const
         if (plain) per_launch = 1;
         for (int b0 = 0; b0 < g.cnt; b0 += (int)per_launch) {
             const int c = (int)std::min<long long>(per_launch, g.cnt - b0);
-            e = ryser_launch_group(p->dtype, g.n, mats, dd + g.at + b0, c, p->partials, out,
-                                   item_status, p->num_sms * 8, st);
+            e = ryser_launch_group(p->dtype, g.n, mats, dd + g.at + b0, c, p->partials, p->d_widths,
+                                   out, item_status, 1 << 30, st);
             if (e != cudaSuccess) return PERM_ECUDA;
         }
     }
@@ -496,6 +535,143 @@ perm_status perm_batch_host(perm_plan_t p, const void* mats, const int* sizes, i
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Autotuner (PERM_FLAG_AUTOTUNE).  Chooses the CTA size and the chain width of
+// the batched Store-zechin kernel by timing every candidate on a synthetic
+// batch of the plan's typical order; every candidate computes bit-identical
+// results (the summation order depends on neither), so tuning never changes a
+// result.  Choices are cached per (device, dtype, order) for the process, and
+// in the file named by LIBPERM_TUNE_CACHE when that is set.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct TuneChoice { int threads; int m_low; float ms; };
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int>, TuneChoice> g_tune;
+
+bool tune_cache_lookup(int dev, int dtype, int n, TuneChoice* c) {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    auto it = g_tune.find(std::make_tuple(dev, dtype, n));
+    if (it != g_tune.end()) { *c = it->second; return true; }
+    const char* path = getenv("LIBPERM_TUNE_CACHE");
+    if (!path) return false;
+    FILE* f = fopen(path, "r");
+    if (!f) return false;
+    char name[256];
+    int fd, fn, th, m;
+    float ms;
+    bool found = false;
+    while (fscanf(f, "%255s %d %d %d %d %f", name, &fd, &fn, &th, &m, &ms) == 6) {
+        if (strcmp(name, "perm-tune") == 0 && fd == dtype && fn == n) {
+            *c = TuneChoice{th, m, ms};
+            found = true;
+        }
+    }
+    fclose(f);
+    if (found) g_tune[std::make_tuple(dev, dtype, n)] = *c;
+    return found;
+}
+
+void tune_cache_store(int dev, int dtype, int n, const TuneChoice& c) {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    g_tune[std::make_tuple(dev, dtype, n)] = c;
+    if (const char* path = getenv("LIBPERM_TUNE_CACHE")) {
+        if (FILE* f = fopen(path, "a")) {
+            fprintf(f, "perm-tune %d %d %d %d %.4f\n", dtype, n, c.threads, c.m_low, c.ms);
+            fclose(f);
+        }
+    }
+}
+
+// Time one candidate on `count` synthetic matrices of order n (device buffers given).
+float time_candidate(int n, perm_dtype dtype, const perm_opts& base, int threads, int m,
+                     const void* d_mats, int count, void* d_out, cudaStream_t st) {
+    perm_opts o = base;
+    o.flags &= ~(PERM_FLAG_AUTOTUNE | PERM_FLAG_GRAPH | PERM_FLAG_PLAIN);
+    o.low_cols = m;
+    o.max_batch = count;
+    o.method = PERM_METHOD_SZ;
+    perm_plan_t p = nullptr;
+    if (plan_create_core(n, dtype, &o, nullptr, 0, threads, &p) != PERM_OK) return -1.f;
+    std::vector<int> sizes(count, n);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float ms = -1.f;
+    bool ok = perm_batch(p, d_mats, sizes.data(), count, d_out, nullptr, st) == PERM_OK;   // warm-up
+    if (ok) {
+        cudaEventRecord(e0, st);
+        ok = perm_batch(p, d_mats, sizes.data(), count, d_out, nullptr, st) == PERM_OK;
+        cudaEventRecord(e1, st);
+    }
+    if (ok && cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    perm_plan_destroy(p);
+    cudaGetLastError();
+    return ok ? ms : -1.f;
+}
+
+}  // namespace
+
+static perm_status plan_create_tuned(int n_max, perm_dtype dtype, const perm_opts* opts,
+                                     perm_plan_t* out) {
+    perm_opts o = *opts;
+    o.flags &= ~PERM_FLAG_AUTOTUNE;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return PERM_ECUDA;
+    // the order the batched kernel is tuned at: the plan's largest batched order, at most 20
+    const int n = std::min(n_max, 20);
+    TuneChoice best{0, 0, 0.f};
+    if (o.method != PERM_METHOD_RYSER && n >= 14 && !o.low_cols && !o.ctas_per_sm &&
+        !tune_cache_lookup(dev, dtype, n, &best)) {
+        const int count = 4 * sms;
+        const size_t eb = dtype == PERM_C128 ? 16 : 8;
+        std::vector<unsigned char> h((size_t)count * n * n * eb);
+        unsigned long long x = 0x9E3779B97F4A7C15ull;   // fixed LCG stream
+        for (size_t i = 0; i < (size_t)count * n * n; i++) {
+            x = x * 6364136223846793005ull + 1442695040888963407ull;
+            if (dtype == PERM_C128) {
+                double* d = reinterpret_cast<double*>(h.data()) + 2 * i;
+                d[0] = ((double)(x >> 11) * 0x1.0p-53 - 0.5) / n;
+                x = x * 6364136223846793005ull + 1442695040888963407ull;
+                d[1] = ((double)(x >> 11) * 0x1.0p-53 - 0.5) / n;
+            } else {
+                reinterpret_cast<long long*>(h.data())[i] = (long long)((x >> 33) & 1ull);
+            }
+        }
+        void *dm = nullptr, *dout = nullptr;
+        cudaStream_t st = nullptr;
+        bool ok = cudaMalloc(&dm, h.size()) == cudaSuccess && cudaMalloc(&dout, (size_t)count * 16) == cudaSuccess &&
+                  cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaMemcpy(dm, h.data(), h.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+        if (ok) {
+            const int thr_c[3] = {256, 384, 512};
+            const int nthr = dtype == PERM_C128 ? 3 : 1;
+            for (int ti = 0; ti < nthr; ti++)
+                for (int m = 11; m <= 13; m++) {
+                    const float ms = time_candidate(n, dtype, o, thr_c[ti], m, dm, count, dout, st);
+                    if (ms > 0.f && (best.ms == 0.f || ms < best.ms)) best = TuneChoice{thr_c[ti], m, ms};
+                }
+        }
+        if (st) cudaStreamDestroy(st);
+        if (dm) cudaFree(dm);
+        if (dout) cudaFree(dout);
+        cudaGetLastError();
+        if (best.ms > 0.f) tune_cache_store(dev, dtype, n, best);
+    }
+    // the tuned chain width applies to the batched path; the one-matrix path keeps its own
+    perm_plan_t p = nullptr;
+    const int code = best.ms > 0.f ? -(best.m_low * 1000 + best.threads) : 0;
+    perm_status s = plan_create_core(n_max, dtype, &o, nullptr, 0, code, &p);
+    if (s != PERM_OK) return s;
+    if (p) p->tuned = best.ms > 0.f;
+    *out = p;
+    return PERM_OK;
+}
 
 // ---------------------------------------------------------------------------
 // FP64 FMA throughput (measurement helper).

@@ -163,7 +163,7 @@ cudaError_t sz_launch_single(int dtype, const void* mats, long long offset, int 
 long long ryser_parts(int dtype, int n);
 size_t ryser_single_workspace_bytes(int dtype, int n);
 cudaError_t ryser_launch_group(int dtype, int n, const void* mats, const ItemDesc* items, int count,
-                               void* partials, void* out, int* item_status, int grid,
+                               void* partials, int* widths, void* out, int* item_status, int grid,
                                cudaStream_t st);
 
 // n = 0 items: per = 1.

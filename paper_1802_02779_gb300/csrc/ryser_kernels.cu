@@ -14,8 +14,10 @@
 // integer path cannot use it because 2^{-(n-1)} does not exist modulo 2^w).
 //
 // Work split.  The 2^G codes of one matrix are cut into `parts` CTA-sized
-// pieces of 2^20 codes (one piece when there are fewer), each piece into 256
-// contiguous thread ranges.  A thread computes its first row sums directly
+// pieces of 2^17 codes (one piece when there are fewer), each piece into 256
+// contiguous thread ranges.  The grid has one CTA per piece, so CTAs retire
+// every few milliseconds and work on higher-priority streams can take their
+// place.  A thread computes its first row sums directly
 // (no drift), then walks its range with one column update per step.  Thread
 // sums are FP64 (complex) or modular; the CTA sums them in double-double in a
 // fixed tree, and a second kernel sums the pieces of each matrix in a fixed
@@ -31,7 +33,7 @@ namespace perm {
 namespace {
 
 constexpr int kRyserThreads = 256;
-constexpr int kLogCodesPerPart = 20;
+constexpr int kLogCodesPerPart = 17;   // one CTA covers 2^17 codes, then retires
 
 __host__ __device__ inline int log_codes(int dtype, int n) {
     return dtype == PERM_C128 ? n - 1 : n;
@@ -213,7 +215,8 @@ __device__ __forceinline__ void ryser_int_range(const long long (*s_col)[N > 0 ?
 template <int N>
 __global__ void __launch_bounds__(kRyserThreads)
 ryser_int_kernel(const long long* __restrict__ mats, const ItemDesc* __restrict__ items,
-                 long long total_parts, int zero_one, IPartial* __restrict__ partials) {
+                 long long total_parts, const int* __restrict__ widths,
+                 IPartial* __restrict__ partials) {
     __shared__ long long s_col[N > 0 ? N : 1][N > 0 ? N : 1];   // s_col[j][i] = a_ij
     __shared__ U128 s_acc[kRyserThreads];
     __shared__ int s_width;
@@ -232,7 +235,7 @@ ryser_int_kernel(const long long* __restrict__ mats, const ItemDesc* __restrict_
             const int i = e / N, j = e % N;
             s_col[j][i] = a[e];
         }
-        if (threadIdx.x == 0) s_width = decide_width(a, N, zero_one != 0);
+        if (threadIdx.x == 0) s_width = widths[task / kParts];
         __syncthreads();
         const int w = s_width;
         U128 acc = {0ull, 0ull};
@@ -311,21 +314,28 @@ __global__ void ryser_finish_int(const ItemDesc* items, long long parts, int cou
     if (item_status) item_status[o] = st;
 }
 
+// Integer width of every matrix of a launch, once (one thread per matrix).
+__global__ void ryser_widths_kernel(const long long* mats, const ItemDesc* items, int count, int n,
+                                    int zero_one, int* widths) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) widths[i] = decide_width(mats + items[i].offset, n, zero_one != 0);
+}
+
 template <int N>
 cudaError_t launch_n(int dtype, const void* mats, const ItemDesc* items, long long total_parts,
-                     void* partials, int grid, cudaStream_t st) {
+                     const int* widths, void* partials, int grid, cudaStream_t st) {
     const int g = (int)std::min<long long>(total_parts, (long long)grid);
     if (dtype == PERM_C128) {
         ryser_c128_kernel<N><<<g, kRyserThreads, 0, st>>>((const double2*)mats, items, total_parts,
                                                           (CPartial*)partials);
     } else {
         ryser_int_kernel<N><<<g, kRyserThreads, 0, st>>>((const long long*)mats, items, total_parts,
-                                                         dtype == PERM_U01, (IPartial*)partials);
+                                                         widths, (IPartial*)partials);
     }
     return cudaGetLastError();
 }
 
-typedef cudaError_t (*launch_fn)(int, const void*, const ItemDesc*, long long, void*, int,
+typedef cudaError_t (*launch_fn)(int, const void*, const ItemDesc*, long long, const int*, void*, int,
                                  cudaStream_t);
 
 template <int... Ns>
@@ -344,14 +354,22 @@ size_t ryser_single_workspace_bytes(int dtype, int n) {
 }
 
 // Launch Ryser for `count` matrices that all have order n (1 <= n <= 40);
-// `partials` holds count * ryser_parts(dtype, n) 32-byte slots.
+// `partials` holds count * ryser_parts(dtype, n) 32-byte slots and `widths`
+// count ints (integer types only).
 cudaError_t ryser_launch_group(int dtype, int n, const void* mats, const ItemDesc* items, int count,
-                               void* partials, void* out, int* item_status, int grid,
+                               void* partials, int* widths, void* out, int* item_status, int grid,
                                cudaStream_t st) {
     if (count <= 0) return cudaSuccess;
     if (n < 1 || n > kMaxN) return cudaErrorInvalidValue;
     const long long parts = parts_for(dtype, n);
-    cudaError_t e = NTable::fns[n - 1](dtype, mats, items, (long long)count * parts, partials, grid, st);
+    if (dtype != PERM_C128) {
+        ryser_widths_kernel<<<(count + 127) / 128, 128, 0, st>>>((const long long*)mats, items, count, n,
+                                                                 dtype == PERM_U01, widths);
+        cudaError_t e0 = cudaGetLastError();
+        if (e0 != cudaSuccess) return e0;
+    }
+    cudaError_t e = NTable::fns[n - 1](dtype, mats, items, (long long)count * parts, widths, partials,
+                                       grid, st);
     if (e != cudaSuccess) return e;
     if (dtype == PERM_C128)
         ryser_finish_c128<<<count, 32, 0, st>>>(items, parts, count, (const CPartial*)partials,

@@ -1,21 +1,25 @@
 // server.cu -- continuous-batching permanent server (host side).
 //
 // Requests of any order and element type arrive through perm_submit and are
-// completed asynchronously.  A worker thread drives two lanes, each with its
+// completed asynchronously.  A worker thread drives three lanes, each with its
 // own CUDA stream, so their work overlaps on the device:
 //
 //   batch lane  orders n <= kSmallN: every pending request of this kind is
 //               taken into the next batch as soon as the previous batch of the
 //               lane has finished (continuous batching); Store-zechin with one
-//               CTA per matrix.
-//   large lane  orders n > kSmallN, one request at a time; the request is
-//               admitted for Store-zechin when its chain tables (the
+//               CTA per matrix.  Highest stream priority.
+//   table lane  orders n > kSmallN whose Store-zechin chain tables (the
 //               "stored sub-permanents" of Section 4 of Su & Zheng,
-//               arXiv:1802.02779) fit the table budget, and is computed with
-//               Ryser's formula (Section 3.3) otherwise.
+//               arXiv:1802.02779) fit the table budget: admitted one at a
+//               time into the budget.  Middle priority.
+//   Ryser lane  the other orders n > kSmallN: Ryser's formula (Section 3.3),
+//               which needs no tables.  Lowest priority.
 //
-// The worker never blocks on the device: it polls events, so a stuck lane
-// cannot hang the host; perm_server_destroy waits at most timeout_ms.
+// The large lanes launch one CTA per chain or per piece of Gray codes, so
+// their CTAs retire every few milliseconds and a batch that arrives on the
+// higher-priority lane takes the freed SM slots first.  The worker never
+// blocks on the device: it polls events, so a stuck lane cannot hang the
+// host; perm_server_destroy waits at most timeout_ms.
 #include "perm_internal.cuh"
 
 #include <algorithm>
@@ -41,6 +45,7 @@ namespace {
 constexpr int kSmallN = 20;
 constexpr int kQueueCap = 1 << 16;
 constexpr int kLaneBatch = 4096;
+constexpr int kLargeLow = 13;      // chain width of the one-matrix Store-zechin path
 
 struct Request {
     uint64_t ticket = 0;
@@ -57,6 +62,8 @@ int dtype_slot(int dtype) { return dtype == PERM_C128 ? 0 : (dtype == PERM_U01 ?
 
 struct Lane {
     cudaStream_t stream = nullptr;
+    int priority = 0;
+    int method = PERM_METHOD_AUTO;
     cudaEvent_t done = nullptr;
     perm_plan_t plans[3] = {nullptr, nullptr, nullptr};   // by dtype slot
     int n_max = 0;
@@ -80,14 +87,14 @@ struct perm_server_s {
     perm_opts opts{};
     std::mutex mu;
     std::condition_variable cv;
-    std::deque<Request*> small_q, large_q;
+    std::deque<Request*> queues[3];
     std::unordered_map<uint64_t, std::unique_ptr<Request>> reqs;
     uint64_t next_ticket = 1;
     int queued = 0;
     std::atomic<bool> stop{false};
     std::atomic<bool> failed{false};
     std::thread worker;
-    Lane lanes[2];
+    Lane lanes[3];
     size_t table_budget = 0;
     int queue_cap = kQueueCap;
 };
@@ -95,7 +102,7 @@ struct perm_server_s {
 namespace {
 
 bool lane_alloc(Lane& L, size_t in_cap, int out_cap) {
-    if (cudaStreamCreateWithFlags(&L.stream, cudaStreamNonBlocking) != cudaSuccess) return false;
+    if (cudaStreamCreateWithPriority(&L.stream, cudaStreamNonBlocking, L.priority) != cudaSuccess) return false;
     if (cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming) != cudaSuccess) return false;
     L.in_cap = in_cap;
     L.out_cap = out_cap;
@@ -131,12 +138,12 @@ perm_plan_t lane_plan(perm_server_t s, Lane& L, int dtype, bool large) {
     if (!L.plans[k]) {
         perm_opts o = s->opts;
         o.flags = 0;
-        o.method = PERM_METHOD_AUTO;
+        o.method = L.method;
         o.max_batch = large ? 1 : kLaneBatch;
         if (!large) o.mem_budget_bytes = 0;   // the table budget applies to the large lane
         perm_plan_t p = nullptr;
         perm_status st;
-        if (large)
+        if (large && L.ext_ws)
             st = plan_create_impl(L.n_max, (perm_dtype)dtype, &o, L.ext_ws, L.ext_ws_bytes, &p);
         else
             st = plan_create_impl(L.n_max, (perm_dtype)dtype, &o, nullptr, 0, &p);
@@ -210,7 +217,7 @@ void worker_loop(perm_server_t s) {
     while (true) {
         bool did = false;
         // completions
-        for (int li = 0; li < 2; li++) {
+        for (int li = 0; li < 3; li++) {
             Lane& L = s->lanes[li];
             if (L.busy) {
                 const cudaError_t q = cudaEventQuery(L.done);
@@ -221,20 +228,20 @@ void worker_loop(perm_server_t s) {
         if (s->failed.load()) {
             // a device error: fail everything that is still queued
             std::lock_guard<std::mutex> g(s->mu);
-            for (auto* q : {&s->small_q, &s->large_q}) {
-                for (Request* r : *q) { r->status = PERM_ECUDA; r->state.store(2, std::memory_order_release); }
-                q->clear();
+            for (auto& q : s->queues) {
+                for (Request* r : q) { r->status = PERM_ECUDA; r->state.store(2, std::memory_order_release); }
+                q.clear();
             }
             s->queued = 0;
         }
         // new batches
-        for (int li = 0; li < 2; li++) {
+        for (int li = 0; li < 3; li++) {
             Lane& L = s->lanes[li];
             if (L.busy || s->failed) continue;
             batch.clear();
             {
                 std::lock_guard<std::mutex> g(s->mu);
-                auto& q = li == 0 ? s->small_q : s->large_q;
+                auto& q = s->queues[li];
                 size_t bytes = 0;
                 const size_t max_items = li == 0 ? (size_t)kLaneBatch : 1;
                 while (!q.empty() && batch.size() < max_items) {
@@ -247,17 +254,17 @@ void worker_loop(perm_server_t s) {
                 s->queued -= (int)batch.size();
             }
             if (!batch.empty()) {
-                if (!lane_launch(s, L, batch, li == 1)) {
+                if (!lane_launch(s, L, batch, li != 0)) {
                     s->failed = true;
                     for (Request* r : batch) { r->status = PERM_ECUDA; r->state.store(2, std::memory_order_release); }
                 }
                 did = true;
             }
         }
-        const bool idle = !s->lanes[0].busy && !s->lanes[1].busy;
+        const bool idle = !s->lanes[0].busy && !s->lanes[1].busy && !s->lanes[2].busy;
         if (s->stop.load() && idle) {
             std::lock_guard<std::mutex> g(s->mu);
-            if (s->small_q.empty() && s->large_q.empty()) break;
+            if (s->queues[0].empty() && s->queues[1].empty() && s->queues[2].empty()) break;
         }
         if (s->stop.load() && s->failed.load()) break;
         if (!did) {
@@ -284,20 +291,28 @@ perm_status perm_server_create(const perm_opts* opts, void* stream, perm_server_
     if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) { delete s; return PERM_ECUDA; }
     s->table_budget = s->opts.mem_budget_bytes ? s->opts.mem_budget_bytes
                                                : std::min<size_t>((size_t)80 << 30, free_b / 3);
+    int least = 0, greatest = 0;
+    cudaDeviceGetStreamPriorityRange(&least, &greatest);
     Lane& small = s->lanes[0];
     Lane& large = s->lanes[1];
+    Lane& ryser = s->lanes[2];
     small.n_max = kSmallN;
-    large.n_max = kMaxN;
+    small.priority = greatest;
+    large.n_max = kMaxNSZ;
+    large.priority = (least + greatest) / 2;
+    ryser.n_max = kMaxN;
+    ryser.priority = least;
+    ryser.method = PERM_METHOD_RYSER;
     bool ok = lane_alloc(small, (size_t)kLaneBatch * kSmallN * kSmallN * 16, kLaneBatch) &&
-              lane_alloc(large, (size_t)kMaxN * kMaxN * 16, 1);
+              lane_alloc(large, (size_t)kMaxN * kMaxN * 16, 1) &&
+              lane_alloc(ryser, (size_t)kMaxN * kMaxN * 16, 1);
     if (ok) {
         large.ext_ws_bytes = s->table_budget;
         ok = cudaMalloc(&large.ext_ws, large.ext_ws_bytes) == cudaSuccess;
     }
     if (!ok) {
         cudaGetLastError();
-        lane_free(small);
-        lane_free(large);
+        for (auto& L : s->lanes) lane_free(L);
         delete s;
         return PERM_ENOMEM;
     }
@@ -324,7 +339,14 @@ perm_status perm_submit(perm_server_t s, const void* host_mat, int n, perm_dtype
         r->ticket = s->next_ticket++;
         *ticket = r->ticket;
         Request* raw = r.get();
-        (n <= kSmallN ? s->small_q : s->large_q).push_back(raw);
+        int lane = 0;
+        if (n > kSmallN) {
+            // admission by table memory: Store-zechin if its chains fit the budget, else Ryser
+            const bool fits = n <= kMaxNSZ &&
+                              sz_matrix_workspace_bytes(dtype, n, kLargeLow) + ((size_t)1 << 20) <= s->table_budget;
+            lane = fits ? 1 : 2;
+        }
+        s->queues[lane].push_back(raw);
         s->queued++;
         s->reqs.emplace(raw->ticket, std::move(r));
     }
@@ -357,7 +379,8 @@ perm_status perm_server_destroy(perm_server_t s, int timeout_ms) {
         bool busy;
         {
             std::lock_guard<std::mutex> g(s->mu);
-            busy = s->lanes[0].busy || s->lanes[1].busy || !s->small_q.empty() || !s->large_q.empty();
+            busy = s->lanes[0].busy || s->lanes[1].busy || s->lanes[2].busy || !s->queues[0].empty() ||
+                   !s->queues[1].empty() || !s->queues[2].empty();
         }
         if (!busy || s->failed.load()) break;
         if (std::chrono::steady_clock::now() >= deadline) { result = PERM_ETIMEDOUT; break; }
@@ -370,8 +393,7 @@ perm_status perm_server_destroy(perm_server_t s, int timeout_ms) {
         return PERM_ETIMEDOUT;
     }
     s->worker.join();
-    lane_free(s->lanes[0]);
-    lane_free(s->lanes[1]);
+    for (auto& L : s->lanes) lane_free(L);
     delete s;
     return result;
 }

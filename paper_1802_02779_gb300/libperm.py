@@ -25,6 +25,7 @@ PERM_C128, PERM_U01, PERM_I64 = 1, 2, 3
 METHOD_AUTO, METHOD_SZ, METHOD_RYSER = 0, 1, 2
 FLAG_PLAIN = 1
 FLAG_GRAPH = 2
+FLAG_AUTOTUNE = 4
 
 DTYPES = {"c128": PERM_C128, "u01": PERM_U01, "i64": PERM_I64}
 
@@ -50,6 +51,7 @@ _SIGS = {
     "perm_plan_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(PermOpts), ctypes.POINTER(_VP)]),
     "perm_plan_destroy": (ctypes.c_int, [_VP]),
     "perm_plan_workspace_bytes": (ctypes.c_size_t, [_VP]),
+    "perm_plan_describe": (ctypes.c_int, [_VP, ctypes.c_char_p, ctypes.c_size_t]),
     "perm_batch": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(ctypes.c_int), ctypes.c_int, _VP, _VP, _VP]),
     "perm_batch_host": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(ctypes.c_int), ctypes.c_int, _VP, _VP, _VP]),
     "perm_server_create": (ctypes.c_int, [ctypes.POINTER(PermOpts), _VP, ctypes.POINTER(_VP)]),
@@ -130,6 +132,12 @@ class Plan:
 
     def workspace_bytes(self) -> int:
         return int(load().perm_plan_workspace_bytes(self._h))
+
+    def describe(self) -> dict:
+        import json
+        buf = ctypes.create_string_buffer(1024)
+        load().perm_plan_describe(self._h, buf, 1024)
+        return json.loads(buf.value.decode())
 
     def close(self):
         if getattr(self, "_h", None) and self._h.value:

@@ -191,3 +191,22 @@ def test_graph_replay(lp, method):
     assert (outs[0][0] == outs[lp.FLAG_GRAPH][0]).all()
     assert (outs[0][1] == outs[lp.FLAG_GRAPH][1]).all()
     assert outs[0][1][3] == outs[0][0][3] * 2 ** 20
+
+
+# ---------------------------------------------------------------------------
+# autotuner: picks a CTA size / chain width, results stay bit-identical
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("dtype", ["c128", "u01"])
+def test_autotuned_plan_same_bits(lp, dtype):
+    n = 16
+    mats = [rand_complex(n, 9100 + k) if dtype == "c128" else rand01(n, 9100 + k) for k in range(40)]
+    with lp.Plan(n, dtype, flags=lp.FLAG_AUTOTUNE) as pt:
+        d = pt.describe()
+        assert d["autotuned"] is True
+        assert d["chain_width_batched"] in (11, 12, 13)
+        tuned = lp.permanents(mats, dtype, plan=pt)
+    plain = lp.permanents(mats, dtype)
+    if dtype == "c128":
+        assert list(tuned) == list(plain)
+    else:
+        assert tuned == plain
