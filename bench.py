@@ -112,6 +112,22 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# DRAM bytes (read + write) per n = 20 complex matrix of sz_batched_c128, from the ncu capture
+# summarised in profiles/sz_batched_c128_n20.md (304 matrices: 29.748599 GB + 7.624131 GB).
+# Valid only for the kernel source it was measured on; otherwise the bench reports null.
+TRAFFIC_C128_PER_MATRIX = (29.748599e9 + 7.624131e9) / 304
+TRAFFIC_SOURCE_SHA256 = "e5e105079b297ec54a6ae5fcbd85b18a1a9d7fb4789be24400718de97a8aa00f"
+
+
+def traffic_per_launch(count: int):
+    import hashlib
+    src = os.path.join(ROOT, "paper_1802_02779_gb300", "csrc", "sz_kernels.cu")
+    with open(src, "rb") as f:
+        if hashlib.sha256(f.read()).hexdigest() != TRAFFIC_SOURCE_SHA256:
+            return None
+    return TRAFFIC_C128_PER_MATRIX * count
+
+
 # ---------------------------------------------------------------------------
 # multi-GPU replicas: max-over-ranks time and the whole-job rate
 # ---------------------------------------------------------------------------
@@ -304,7 +320,8 @@ def run_gpu(args, rank, world):
                 "peak_source": "measured this run by perm_measure_fp64_peak (independent DFMA chains, all SMs)",
                 "work_per_permanent_flops": sz_c128_flops(N),
                 "standard_count_flops_per_permanent": sz_c128_standard_flops(N),
-                "traffic": None}
+                "traffic": traffic_per_launch(count),
+                "traffic_unit": "bytes per launch (ncu dram__bytes_read+write, scaled per matrix)"}
 
     extras = {}
     if not args.no_extras:
