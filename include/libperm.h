@@ -30,7 +30,9 @@
  *
  * Conventions
  *   - Matrices of one call are concatenated: matrix i starts at element
- *     offset_i = sum_{j<i} n_j^2 of `mats`.
+ *     offset_i = sum_{j<i} n_j^2 of `mats`.  Device buffers must be aligned to
+ *     their element type (16 bytes for complex128 -- as torch and cudaMalloc
+ *     give them).
  *   - n = 0 is allowed and gives per = 1 (empty product).  1 <= n <= 34 may use
  *     Store-zechin; Ryser accepts n <= 40 (complex) and n <= 40 (integers).
  *   - Results: PERM_C128 -> double2 out[count] (re, im).  Integer types ->
@@ -169,6 +171,21 @@ perm_status perm_submit(perm_server_t server, const void *host_mat, int n, perm_
                         uint64_t *ticket);
 perm_status perm_poll(perm_server_t server, uint64_t ticket, void *out16, int *item_status);
 perm_status perm_server_destroy(perm_server_t server, int timeout_ms);
+
+/* Amplitudes of all collision-free output patterns of boson-sampling inputs in
+   one Store-zechin pass (Section 2: an amplitude is the permanent of the
+   submatrix of the input rows and the pattern's output columns; Section 4's
+   stored sub-permanents of the rows x cols matrix at level `rows` are exactly
+   those permanents).
+     mats   device pointer, `count` complex128 matrices of rows x cols, row-major
+            (the input rows of the unitary restricted to the output modes)
+     out    device pointer, count * C(cols, rows) double2: for matrix i, entry r is
+            the permanent of the rows x rows submatrix whose columns are the r-th
+            rows-subset of {0..cols-1} in colex order (subsets ordered by their
+            largest element, then the next largest, ...)
+   1 <= rows <= cols <= 13.  Each value is bit-identical to perm_batch on that
+   submatrix.  Asynchronous on `stream`; PERM_EINVAL for bad sizes/pointers. */
+perm_status perm_patterns(const void *mats, int count, int rows, int cols, void *out, void *stream);
 
 /* Store-zechin permanent of ONE matrix without allocating any device memory.
    The paper has no counterpart to this entry point; it exists for callers that

@@ -62,6 +62,7 @@ _SIGS = {
     "perm_version": (ctypes.c_char_p, []),
     "perm_measure_fp64_peak": (ctypes.c_int, [ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
     "perm_sz_noalloc": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP, _VP, _VP]),
+    "perm_patterns": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _VP]),
 }
 
 _lib = None
@@ -175,6 +176,31 @@ class Plan:
                                     _VP(item_status.ctypes.data if item_status is not None else 0),
                                     _VP(_stream_ptr(stream) if stream is not None else 0))
         _check(rc, "perm_batch_host")
+
+
+def colex_subsets(cols: int, rows: int):
+    """The rows-subsets of range(cols) in colex order (the order perm_patterns uses)."""
+    import itertools
+    subs = list(itertools.combinations(range(cols), rows))
+    return sorted(subs, key=lambda c: tuple(reversed(c)))
+
+
+def patterns(mats, stream=None):
+    """All collision-free pattern amplitudes of rows x cols complex matrices (host in/out).
+
+    Returns an array (count, C(cols, rows)) ordered like colex_subsets(cols, rows)."""
+    import math
+    import torch
+    mats = np.ascontiguousarray(np.asarray(mats, dtype=np.complex128))
+    if mats.ndim == 2:
+        mats = mats[None]
+    count, rows, cols = mats.shape
+    dev = torch.from_numpy(mats.reshape(-1)).cuda()
+    out = torch.empty(count * math.comb(cols, rows), dtype=torch.complex128, device="cuda")
+    _check(load().perm_patterns(_VP(dev.data_ptr()), count, rows, cols, _VP(out.data_ptr()),
+                                _VP(_stream_ptr(stream))), "perm_patterns")
+    torch.cuda.synchronize()
+    return out.cpu().numpy().reshape(count, -1)
 
 
 def u128_to_int(lo_hi) -> int:

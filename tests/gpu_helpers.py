@@ -20,7 +20,7 @@ def tol_c(m) -> float:
 def rand_complex(n, seed, scale=None):
     g = np.random.default_rng(seed)
     z = (g.standard_normal((n, n)) + 1j * g.standard_normal((n, n))) / np.sqrt(2.0)
-    return z * (scale if scale is not None else 1.0 / np.sqrt(n))
+    return z * (scale if scale is not None else 1.0 / np.sqrt(max(n, 1)))
 
 
 def rand01(n, seed, p=0.5):

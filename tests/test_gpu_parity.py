@@ -210,3 +210,31 @@ def test_autotuned_plan_same_bits(lp, dtype):
         assert list(tuned) == list(plain)
     else:
         assert tuned == plain
+
+
+# ---------------------------------------------------------------------------
+# all collision-free patterns in one pass (perm_patterns)
+# ---------------------------------------------------------------------------
+def test_patterns_five_boson(lp):
+    """rows 0..4 of the 9x9 Haar unitary: one 5x9 pass gives all 126 amplitudes,
+    bit-identical to the 126 separate 5x5 permanents."""
+    u = wl.haar_unitary(9, 18021)
+    got = lp.patterns(u[:5])[0]
+    subs = lp.colex_subsets(9, 5)
+    assert len(got) == 126
+    sep = lp.permanents([np.ascontiguousarray(u[:5][:, list(c)]) for c in subs], "c128")
+    assert list(got) == list(sep)
+    for c, g in zip(subs[:20], got[:20]):
+        m = np.ascontiguousarray(u[:5][:, list(c)])
+        assert abs(g - oracle_c(m)) <= tol_c(m)
+
+
+@pytest.mark.parametrize("rows,cols", [(1, 4), (3, 3), (4, 11), (6, 13)])
+def test_patterns_shapes(lp, rows, cols):
+    g = np.random.default_rng(rows * 100 + cols)
+    mats = (g.standard_normal((3, rows, cols)) + 1j * g.standard_normal((3, rows, cols))) / np.sqrt(2 * cols)
+    got = lp.patterns(mats)
+    subs = lp.colex_subsets(cols, rows)
+    for i in range(3):
+        sep = lp.permanents([np.ascontiguousarray(mats[i][:, list(c)]) for c in subs], "c128")
+        assert list(got[i]) == list(sep)
