@@ -392,9 +392,46 @@ def measure_extras(lp, torch, cm, im, stream, c_kernel_ms, count):
             res[name + "_value"] = [float(o32[0].real), float(o32[0].imag)]
     res["sz_fp64_tflops"] = sz_c128_flops(32) / (res["store_zechin_ms"] / 1000.0) / 1e12
     out["n32"] = res
+    out["five_boson"] = measure_five_boson(lp, torch, stream)
     out["uneven"] = measure_uneven(lp, torch, stream)
     out["serving"] = measure_serving(lp)
     return out
+
+
+def measure_five_boson(lp, torch, stream, reps=20):
+    """5-boson sampling: the 126 collision-free 5x5 submatrices of rows 0..4 of a
+    9x9 Haar unitary and 100 Bernoulli(0.5) 5x5 0/1 matrices; latency of one call
+    per method (CUDA events, median of `reps`), and all 126 amplitudes from one
+    5x9 Store-zechin pass (perm_patterns)."""
+    from paper_1802_02779_gb300 import workloads as wl
+    cm, im = wl.five_boson()
+    dc = torch.from_numpy(np.ascontiguousarray(cm).reshape(-1)).cuda()
+    di = torch.from_numpy(np.ascontiguousarray(im).reshape(-1)).cuda()
+    oc = torch.empty(len(cm), dtype=torch.complex128, device="cuda")
+    oi = torch.empty((len(im), 2), dtype=torch.int64, device="cuda")
+    u9 = torch.from_numpy(np.ascontiguousarray(wl.haar_unitary(9, wl.SEED_BASE + 1)[:5]).reshape(-1)).cuda()
+    op = torch.empty(126, dtype=torch.complex128, device="cuda")
+
+    def timed(fn):
+        ts = []
+        for _ in range(reps + 2):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) * 1000.0)
+        return float(np.median(ts[2:]))
+
+    res = {"complex": len(cm), "zero_one": len(im)}
+    for name, meth in (("store_zechin", lp.METHOD_SZ), ("ryser", lp.METHOD_RYSER)):
+        with lp.Plan(5, "c128", method=meth) as pc, lp.Plan(5, "u01", method=meth) as pi:
+            res[name + "_complex_us"] = timed(lambda: pc.batch(dc, [5] * len(cm), oc, None, stream))
+            res[name + "_zero_one_us"] = timed(lambda: pi.batch(di, [5] * len(im), oi, None, stream))
+    lib = lp.load()
+    res["patterns_one_pass_us"] = timed(lambda: lib.perm_patterns(
+        lp._VP(u9.data_ptr()), 1, 5, 9, lp._VP(op.data_ptr()), lp._VP(stream.cuda_stream)))
+    return res
 
 
 def measure_uneven(lp, torch, stream, count=1000):

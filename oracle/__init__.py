@@ -37,8 +37,6 @@ _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-MASK256 = (1 << 256) - 1
-
 
 def build(force: bool = False, out_path: str = None, defines=()) -> str:
     """Compile ``perm_oracle.c`` into ``liboracle.so`` next to it (gcc, OpenMP).

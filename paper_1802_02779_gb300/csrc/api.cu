@@ -58,6 +58,7 @@ struct perm_plan_s {
     int m_low = 12;               // chain width of the batched kernel (two CTAs per SM)
     int m_single = 13;            // chain width of the one-matrix-over-the-GPU path
     int c128_threads = 384;       // CTA size of the batched complex kernel
+    int int_threads = 256;        // CTA size of the batched integer kernel
     size_t budget = 0;
 
     // Store-zechin
@@ -189,7 +190,8 @@ static perm_status plan_create_core(int n_max, perm_dtype dtype, const perm_opts
         p->m_low = code / 1000;
         threads = code % 1000;
     }
-    if (threads && sz_c128_threads_valid(threads)) p->c128_threads = threads;
+    if (threads && dtype == PERM_C128 && sz_c128_threads_valid(threads)) p->c128_threads = threads;
+    if (threads && dtype != PERM_C128 && sz_int_threads_valid(threads)) p->int_threads = threads;
     cudaError_t e = cudaGetDevice(&p->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
     size_t free_b = 0, total_b = 0;
@@ -206,7 +208,7 @@ static perm_status plan_create_core(int n_max, perm_dtype dtype, const perm_opts
         if (sz_init_tables() != cudaSuccess) { delete p; return PERM_ECUDA; }
         int per_sm = o.ctas_per_sm ? o.ctas_per_sm
                                    : sz_batched_occupancy(dtype, std::max(1, p->sz_batch_nmax), p->m_low,
-                                                          p->c128_threads);
+                                                          dtype == PERM_C128 ? p->c128_threads : p->int_threads);
         p->sz_grid = p->num_sms * per_sm;
         sz_batched = p->sz_ws_per_cta * (size_t)p->sz_grid;
         // largest n whose single-matrix workspace fits the remaining budget
@@ -292,10 +294,11 @@ int perm_plan_describe(perm_plan_t p, char* buf, size_t len) {
     return snprintf(buf, len,
                     "{\"dtype\": \"%s\", \"n_max\": %d, \"method\": %d, \"flags\": %u, "
                     "\"sz_batch_nmax\": %d, \"sz_single_nmax\": %d, \"chain_width_batched\": %d, "
-                    "\"chain_width_single\": %d, \"complex_cta_threads\": %d, \"batched_grid\": %d, "
+                    "\"chain_width_single\": %d, \"cta_threads\": %d, \"batched_grid\": %d, "
                     "\"workspace_bytes\": %zu, \"autotuned\": %s}",
                     dt, p->n_max, p->method, p->flags, p->sz_batch_nmax, p->sz_single_nmax, p->m_low,
-                    p->m_single, p->c128_threads, p->sz_grid, perm_plan_workspace_bytes(p),
+                    p->m_single, p->dtype == PERM_C128 ? p->c128_threads : p->int_threads, p->sz_grid,
+                    perm_plan_workspace_bytes(p),
                     p->tuned ? "true" : "false");
 }
 
@@ -372,8 +375,8 @@ perm_status enqueue(perm_plan_t p, const BatchLayout& L, const void* mats, const
         if (e != cudaSuccess) return PERM_ECUDA;
         const int grid = std::min<int>(p->sz_grid, (int)L.nszb);
         e = sz_launch_batched(p->dtype, mats, dd + L.szb_at, (int)L.nszb, L.szb_nmax, p->m_low,
-                              p->c128_threads, out, item_status, p->ws, p->sz_ws_per_cta, grid,
-                              p->d_counter, st);
+                              p->dtype == PERM_C128 ? p->c128_threads : p->int_threads, out, item_status,
+                              p->ws, p->sz_ws_per_cta, grid, p->d_counter, st);
         if (e != cudaSuccess) return PERM_ECUDA;
     }
     for (auto& d : L.szs) {
@@ -650,11 +653,13 @@ static perm_status plan_create_tuned(int n_max, perm_dtype dtype, const perm_opt
                   cudaMemcpy(dm, h.data(), h.size(), cudaMemcpyHostToDevice) == cudaSuccess;
         if (ok) {
             const int thr_c[3] = {256, 384, 512};
-            const int nthr = dtype == PERM_C128 ? 3 : 1;
+            const int thr_i[2] = {256, 512};
+            const int* thr = dtype == PERM_C128 ? thr_c : thr_i;
+            const int nthr = dtype == PERM_C128 ? 3 : 2;
             for (int ti = 0; ti < nthr; ti++)
                 for (int m = 11; m <= 13; m++) {
-                    const float ms = time_candidate(n, dtype, o, thr_c[ti], m, dm, count, dout, st);
-                    if (ms > 0.f && (best.ms == 0.f || ms < best.ms)) best = TuneChoice{thr_c[ti], m, ms};
+                    const float ms = time_candidate(n, dtype, o, thr[ti], m, dm, count, dout, st);
+                    if (ms > 0.f && (best.ms == 0.f || ms < best.ms)) best = TuneChoice{thr[ti], m, ms};
                 }
         }
         if (st) cudaStreamDestroy(st);

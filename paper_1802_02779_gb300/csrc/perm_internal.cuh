@@ -67,7 +67,6 @@ __device__ __forceinline__ dd2 dd_add_prod(dd2 x, double a, double b) {
     double e = __fma_rn(a, b, -p);
     return dd_add(x, dd2{p, e});
 }
-__device__ __forceinline__ dd2 dd_add_d(dd2 x, double a) { return dd_add(x, dd2{a, 0.0}); }
 __device__ __forceinline__ double dd_round(dd2 x) { return __dadd_rn(x.hi, x.lo); }
 
 // ---------------------------------------------------------------------------
@@ -141,9 +140,9 @@ __device__ __forceinline__ int width_status(int w) {
 size_t sz_chain_words(int dtype, int m);                 // 64-bit words per chain
 size_t sz_matrix_workspace_bytes(int dtype, int n, int m);
 int sz_smem_bytes(int dtype, int n, int m);                // dynamic shared memory per CTA
-int sz_threads(int dtype);
 int sz_batched_occupancy(int dtype, int n_max, int m, int threads);   // resident CTAs per SM
 int sz_c128_threads_valid(int threads);
+int sz_int_threads_valid(int threads);
 cudaError_t sz_init_tables();                              // once per device (idempotent)
 
 // Batched: one CTA per matrix, persistent over `count` items (dynamic order by
@@ -161,7 +160,6 @@ cudaError_t sz_launch_single(int dtype, const void* mats, long long offset, int 
 // Ryser: every matrix's codes are cut into ryser_parts(dtype, n) CTA-sized
 // pieces (a function of n only).  One launch per distinct order n.
 long long ryser_parts(int dtype, int n);
-size_t ryser_single_workspace_bytes(int dtype, int n);
 cudaError_t ryser_launch_group(int dtype, int n, const void* mats, const ItemDesc* items, int count,
                                void* partials, int* widths, void* out, int* item_status, int grid,
                                cudaStream_t st);
@@ -170,6 +168,5 @@ cudaError_t ryser_launch_group(int dtype, int n, const void* mats, const ItemDes
 cudaError_t launch_trivial(int dtype, const ItemDesc* items, int count, void* out,
                            int* item_status, cudaStream_t st);
 
-unsigned long long binom_host(int n, int k);
 
 }  // namespace perm

@@ -349,9 +349,6 @@ using NTable = Table<PERM_NS>;
 
 }  // namespace
 
-size_t ryser_single_workspace_bytes(int dtype, int n) {
-    return (size_t)parts_for(dtype, n) * 32;
-}
 
 // Launch Ryser for `count` matrices that all have order n (1 <= n <= 40);
 // `partials` holds count * ryser_parts(dtype, n) 32-byte slots and `widths`

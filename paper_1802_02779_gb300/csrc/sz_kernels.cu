@@ -60,7 +60,6 @@ namespace perm {
 namespace {
 
 constexpr int kBinomDim = 24;            // C(x, y) for x < 24 (t <= 21, m <= 13)
-constexpr int kThreadsC128 = 384;         // batched: two CTAs per SM
 constexpr int kThreadsC128Single = 512;   // one matrix over the whole GPU: one CTA per SM
 constexpr int kThreadsInt = 256;          // integers: up to four CTAs per SM
 constexpr int kMaskTableLen = (2 << kMaxLow) - 2;   // sum_{m=1..13} 2^m
@@ -538,9 +537,10 @@ sz_batched_c128(const double2* __restrict__ mats, const ItemDesc* __restrict__ i
 }
 
 // W64ONLY: the host guarantees every item fits 64 bits (0/1 input, n <= 20),
-// so the chain needs only one word per entry.
-template <bool ZO, bool W64ONLY>
-__global__ void __launch_bounds__(kThreadsInt, 3)
+// so the chain needs only one word per entry.  THREADS: 256 (up to four CTAs
+// per SM) or 512 (two).
+template <bool ZO, bool W64ONLY, int THREADS>
+__global__ void __launch_bounds__(THREADS, THREADS == 256 ? 3 : 2)
 sz_batched_int(const long long* __restrict__ mats, const ItemDesc* __restrict__ items, int count,
                int m_param, unsigned long long* out, int* item_status,
                unsigned long long* workspace, size_t ws_words_per_cta, unsigned* counter) {
@@ -657,11 +657,16 @@ __global__ void trivial_kernel(int dtype, const ItemDesc* items, int count, void
 typedef void (*int_batched_fn)(const long long*, const ItemDesc*, int, int, unsigned long long*, int*,
                                unsigned long long*, size_t, unsigned*);
 
-int_batched_fn pick_int_batched(int dtype, int n_max) {
+template <int T>
+int_batched_fn pick_int_batched_t(int dtype, int n_max) {
     const bool zo = dtype == PERM_U01;
-    if (zo && n_max <= 20) return sz_batched_int<true, true>;     // 20! < 2^64
-    if (zo) return sz_batched_int<true, false>;
-    return sz_batched_int<false, false>;
+    if (zo && n_max <= 20) return sz_batched_int<true, true, T>;     // 20! < 2^64
+    if (zo) return sz_batched_int<true, false, T>;
+    return sz_batched_int<false, false, T>;
+}
+
+int_batched_fn pick_int_batched(int dtype, int n_max, int threads) {
+    return threads == 512 ? pick_int_batched_t<512>(dtype, n_max) : pick_int_batched_t<256>(dtype, n_max);
 }
 
 int batched_kind(int dtype, int n_max) {
@@ -678,8 +683,6 @@ cudaError_t set_smem(const void* fn, int bytes) {
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
-unsigned long long binom_host(int n, int k) { return binom_calc(n, k); }
-
 cudaError_t sz_init_tables() {
     // once per device: the mask lists, ordered by (popcount, value), for m = 1..kMaxLow
     static std::mutex mu;
@@ -718,7 +721,6 @@ int sz_smem_bytes(int dtype, int n, int m_param) {
     return smem_layout(kU128, n, m).total;
 }
 
-int sz_threads(int dtype) { return dtype == PERM_C128 ? kThreadsC128 : kThreadsInt; }
 
 // Batched complex kernel variants by CTA size.
 static const void* c128_batched_fn(int threads) {
@@ -729,15 +731,17 @@ static const void* c128_batched_fn(int threads) {
     }
 }
 int sz_c128_threads_valid(int threads) { return threads == 256 || threads == 384 || threads == 512; }
+int sz_int_threads_valid(int threads) { return threads == 256 || threads == 512; }
 
 // Resident CTAs per SM of the batched kernel for a batch whose largest order is n_max.
 int sz_batched_occupancy(int dtype, int n_max, int m_param, int threads) {
     const int m = sz_low_for(n_max, m_param);
     const int kind = batched_kind(dtype, n_max);
     const int smem = smem_layout(kind, n_max, m).total;
+    const int ithreads = sz_int_threads_valid(threads) ? threads : kThreadsInt;
     const void* fn = dtype == PERM_C128 ? c128_batched_fn(threads)
-                                        : (const void*)pick_int_batched(dtype, n_max);
-    const int nthr = dtype == PERM_C128 ? threads : kThreadsInt;
+                                        : (const void*)pick_int_batched(dtype, n_max, ithreads);
+    const int nthr = dtype == PERM_C128 ? threads : ithreads;
     if (set_smem(fn, smem) != cudaSuccess) return 1;
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, nthr, smem) != cudaSuccess)
@@ -769,10 +773,11 @@ cudaError_t sz_launch_batched(int dtype, const void* mats, const ItemDesc* items
         else
             sz_batched_c128<384><<<grid, 384, smem, st>>>(a0, items, count, m, o0, item_status, w0, wpc, counter);
     } else {
-        int_batched_fn fn = pick_int_batched(dtype, n_max);
+        const int ithreads = sz_int_threads_valid(threads) ? threads : kThreadsInt;
+        int_batched_fn fn = pick_int_batched(dtype, n_max, ithreads);
         e = set_smem((const void*)fn, smem);
         if (e != cudaSuccess) return e;
-        fn<<<grid, kThreadsInt, smem, st>>>((const long long*)mats, items, count, m,
+        fn<<<grid, ithreads, smem, st>>>((const long long*)mats, items, count, m,
                                             (unsigned long long*)out, item_status,
                                             (unsigned long long*)workspace, ws_per_cta / 8, counter);
     }
