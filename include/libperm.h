@@ -187,6 +187,22 @@ perm_status perm_server_destroy(perm_server_t server, int timeout_ms);
    submatrix.  Asynchronous on `stream`; PERM_EINVAL for bad sizes/pointers. */
 perm_status perm_patterns(const void *mats, int count, int rows, int cols, void *out, void *stream);
 
+/* Amplitudes of ALL output patterns, collisions included, in one pass.  An
+   output pattern of `rows` photons in `cols` modes is a multiset M (mode j
+   occupied t_j times); its amplitude is the permanent of the rows x rows matrix
+   of the input rows and the columns of M with repetition (probability
+   |per|^2 / prod_j t_j!).  Developing along a row (Section 3.1, property 4)
+   gives T_k[M] = sum_{j in M} t_j a[k-1][j] T_{k-1}[M - j], which is evaluated
+   level by level.
+     out   count * C(cols + rows - 1, rows) double2; entry r of matrix i is the
+           multiset whose sorted modes m_0 <= ... <= m_{rows-1} map to the r-th
+           rows-subset {m_p + p} of {0..cols+rows-2} in colex order
+   1 <= rows, cols <= 13 and 2 * C(cols + rows - 1, rows) <= 12000 (two levels in
+   shared memory), else PERM_EINVAL.  Complex128, FP64 (last level
+   double-double); asynchronous on `stream`. */
+perm_status perm_patterns_multiset(const void *mats, int count, int rows, int cols, void *out,
+                                   void *stream);
+
 /* Store-zechin permanent of ONE matrix without allocating any device memory.
    The paper has no counterpart to this entry point; it exists for callers that
    cannot call cudaMalloc: code running inside a framework whose pool owns all

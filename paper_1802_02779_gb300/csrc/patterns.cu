@@ -37,6 +37,13 @@ __host__ __device__ inline PatLayout pat_layout(int rows, int cols) {
     return L;
 }
 
+unsigned pat_binom_host(int n, int k) {
+    if (k < 0 || k > n) return 0;
+    unsigned long long r = 1;
+    for (int i = 1; i <= k; i++) r = r * (unsigned long long)(n - k + i) / (unsigned long long)i;
+    return (unsigned)r;
+}
+
 __device__ __forceinline__ unsigned pat_binom(int n, int k) {
     if (k < 0 || k > n) return 0;
     unsigned r = 1;
@@ -142,6 +149,122 @@ extern "C" perm_status perm_patterns(const void* mats, int count, int rows, int 
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return PERM_ECUDA;
     patterns_c128<<<count, kPatThreads, smem, (cudaStream_t)stream>>>(
+        (const double2*)mats, count, rows, cols, (double2*)out);
+    return cudaGetLastError() == cudaSuccess ? PERM_OK : PERM_ECUDA;
+}
+
+// ---------------------------------------------------------------------------
+// All output patterns WITH collisions (repeated output modes).
+//
+// An output pattern of r photons over c modes is a multiset M (mode j occupied
+// t_j times, sum t_j = r); its amplitude is the permanent of the r x r matrix of
+// the input rows and the columns of M with repetition, and its probability is
+// |per|^2 / prod_j t_j!.  Developing along row k-1 as in Section 3.1 (property
+// 4), the t_j positions that hold mode j give identical minors, so
+//     T_k[M] = sum_{j in M, ascending} t_j * a[k-1][j] * T_{k-1}[M - j],
+// the Store-zechin recurrence over multisets.  Multisets of size k are ranked
+// through the bijection M = (m_0 <= ... <= m_{k-1})  <->  {m_i + i}, a k-subset
+// of {0..c+k-2}, in colex order.  Two levels live in shared memory.
+// ---------------------------------------------------------------------------
+namespace perm {
+namespace {
+
+constexpr int kMsMaxEntries = 12000;     // entries (16 B each) of the two live levels
+
+__device__ __forceinline__ unsigned ms_binom(int n, int k) { return pat_binom(n, k); }
+
+// multiset of size k over c modes with colex rank r -> counts in `cnt` (c entries)
+__device__ inline void ms_unrank(unsigned r, int k, int c, unsigned char* cnt) {
+    for (int j = 0; j < c; j++) cnt[j] = 0;
+    int x = c + k - 2;
+    for (int p = k - 1; p >= 0; p--) {
+        while (ms_binom(x, p + 1) > r) x--;
+        r -= ms_binom(x, p + 1);
+        cnt[x - p]++;                    // element p of the subset is m_p + p
+        x--;
+    }
+}
+
+// colex rank of the multiset given by counts (size k)
+__device__ inline unsigned ms_rank(const unsigned char* cnt, int c) {
+    unsigned r = 0;
+    int p = 0;
+    for (int j = 0; j < c; j++)
+        for (int q = 0; q < cnt[j]; q++, p++) r += ms_binom(j + p, p + 1);
+    return r;
+}
+
+__global__ void __launch_bounds__(kPatThreads)
+patterns_multiset_c128(const double2* __restrict__ mats, int count, int rows, int cols,
+                       double2* out) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int item = blockIdx.x;
+    if (item >= count) return;
+    const double2* a = mats + (size_t)item * rows * cols;
+    const unsigned lvl_max = ms_binom(cols + rows - 1, rows);
+    double2* cxy = reinterpret_cast<double2*>(smem);                      // rows * cols
+    double2* buf0 = reinterpret_cast<double2*>(smem + 16 * rows * cols);   // level k-1
+    double2* buf1 = buf0 + lvl_max;                                        // level k
+    for (int e = threadIdx.x; e < rows * cols; e += blockDim.x) cxy[e] = a[e];
+    if (threadIdx.x == 0) buf0[0] = make_double2(1.0, 0.0);               // T_0 = 1
+    __syncthreads();
+    double2* prev = buf0;
+    double2* cur = buf1;
+    double2* o = out + (size_t)item * lvl_max;
+    for (int k = 1; k <= rows; k++) {
+        const unsigned cntk = ms_binom(cols + k - 1, k);
+        const double2* rxy = cxy + (k - 1) * cols;
+        for (unsigned r = threadIdx.x; r < cntk; r += blockDim.x) {
+            unsigned char t[kPatMaxCols];
+            ms_unrank(r, k, cols, t);
+            double re = 0.0, im = 0.0;
+            dd2 dre = {0.0, 0.0}, dim = {0.0, 0.0};
+            for (int j = 0; j < cols; j++) {
+                if (!t[j]) continue;
+                t[j]--;
+                const double2 p = prev[ms_rank(t, cols)];
+                t[j]++;
+                const double m = (double)t[j];
+                const double cx = m * rxy[j].x, cy = m * rxy[j].y;   // t_j * a[k-1][j]
+                if (k < rows) {
+                    re = __fma_rn(cx, p.x, re);
+                    re = __fma_rn(-cy, p.y, re);
+                    im = __fma_rn(cx, p.y, im);
+                    im = __fma_rn(cy, p.x, im);
+                } else {
+                    dre = dd_add_prod(dre, cx, p.x);
+                    dre = dd_add_prod(dre, -cy, p.y);
+                    dim = dd_add_prod(dim, cx, p.y);
+                    dim = dd_add_prod(dim, cy, p.x);
+                }
+            }
+            const double2 v = k < rows ? make_double2(re, im) : make_double2(dd_round(dre), dd_round(dim));
+            cur[r] = v;
+            if (k == rows) o[r] = v;
+        }
+        __syncthreads();
+        double2* tmp = prev;
+        prev = cur;
+        cur = tmp;
+    }
+}
+
+}  // namespace
+}  // namespace perm
+
+extern "C" perm_status perm_patterns_multiset(const void* mats, int count, int rows, int cols,
+                                              void* out, void* stream) {
+    using namespace perm;
+    if (count < 0 || rows < 1 || cols < 1 || cols > kPatMaxCols || rows > kPatMaxCols) return PERM_EINVAL;
+    const unsigned lvl_max = pat_binom_host(cols + rows - 1, rows);
+    if (2ull * lvl_max > (unsigned long long)kMsMaxEntries) return PERM_EINVAL;
+    if (count == 0) return PERM_OK;
+    if (!mats || !out) return PERM_EINVAL;
+    const int smem = 16 * rows * cols + 16 * 2 * (int)lvl_max;
+    cudaError_t e = cudaFuncSetAttribute((const void*)patterns_multiset_c128,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return PERM_ECUDA;
+    patterns_multiset_c128<<<count, kPatThreads, smem, (cudaStream_t)stream>>>(
         (const double2*)mats, count, rows, cols, (double2*)out);
     return cudaGetLastError() == cudaSuccess ? PERM_OK : PERM_ECUDA;
 }

@@ -63,6 +63,7 @@ _SIGS = {
     "perm_measure_fp64_peak": (ctypes.c_int, [ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
     "perm_sz_noalloc": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP, _VP, _VP]),
     "perm_patterns": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _VP]),
+    "perm_patterns_multiset": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _VP]),
 }
 
 _lib = None
@@ -199,6 +200,37 @@ def patterns(mats, stream=None):
     out = torch.empty(count * math.comb(cols, rows), dtype=torch.complex128, device="cuda")
     _check(load().perm_patterns(_VP(dev.data_ptr()), count, rows, cols, _VP(out.data_ptr()),
                                 _VP(_stream_ptr(stream))), "perm_patterns")
+    torch.cuda.synchronize()
+    return out.cpu().numpy().reshape(count, -1)
+
+
+def colex_multisets(cols: int, rows: int):
+    """Occupation vectors (t_0..t_{cols-1}) of the outputs of perm_patterns_multiset, in order."""
+    import itertools
+    subs = sorted(itertools.combinations(range(cols + rows - 1), rows), key=lambda c: tuple(reversed(c)))
+    out = []
+    for sub in subs:
+        t = [0] * cols
+        for p, x in enumerate(sub):
+            t[x - p] += 1
+        out.append(tuple(t))
+    return out
+
+
+def patterns_multiset(mats, stream=None):
+    """All output-pattern amplitudes (collisions included) of rows x cols complex
+    matrices (host in/out): array (count, C(cols+rows-1, rows)) ordered like
+    colex_multisets(cols, rows)."""
+    import math
+    import torch
+    mats = np.ascontiguousarray(np.asarray(mats, dtype=np.complex128))
+    if mats.ndim == 2:
+        mats = mats[None]
+    count, rows, cols = mats.shape
+    dev = torch.from_numpy(mats.reshape(-1)).cuda()
+    out = torch.empty(count * math.comb(cols + rows - 1, rows), dtype=torch.complex128, device="cuda")
+    _check(load().perm_patterns_multiset(_VP(dev.data_ptr()), count, rows, cols, _VP(out.data_ptr()),
+                                         _VP(_stream_ptr(stream))), "perm_patterns_multiset")
     torch.cuda.synchronize()
     return out.cpu().numpy().reshape(count, -1)
 

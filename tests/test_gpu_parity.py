@@ -238,3 +238,31 @@ def test_patterns_shapes(lp, rows, cols):
     for i in range(3):
         sep = lp.permanents([np.ascontiguousarray(mats[i][:, list(c)]) for c in subs], "c128")
         assert list(got[i]) == list(sep)
+
+
+def test_patterns_with_collisions_sum_rule(lp):
+    """All 1287 outputs of 5 photons in 9 modes (collisions included) in one pass:
+    the probabilities |per|^2 / prod t_j! sum to 1 (a unitary), each amplitude
+    matches the oracle, and the collision-free ones match perm_patterns."""
+    import math
+    u = wl.haar_unitary(9, 18021)
+    amps = lp.patterns_multiset(u[:5])[0]
+    occ = lp.colex_multisets(9, 5)
+    assert len(amps) == len(occ) == 1287
+    total = sum(abs(a) ** 2 / np.prod([math.factorial(t) for t in o]) for a, o in zip(amps, occ))
+    assert abs(total - 1.0) < 1e-12
+    for idx in np.random.default_rng(9).choice(len(occ), size=40, replace=False):
+        cols = [j for j, t in enumerate(occ[idx]) for _ in range(t)]
+        m = np.ascontiguousarray(u[:5][:, cols])
+        assert abs(amps[idx] - oracle_c(m)) <= tol_c(m)
+    free = lp.patterns(u[:5])[0]
+    free_occ = [tuple(1 if j in c else 0 for j in range(9)) for c in lp.colex_subsets(9, 5)]
+    lookup = dict(zip(occ, amps))
+    for o, f in zip(free_occ, free):
+        assert abs(lookup[o] - f) <= 1e-14
+
+
+def test_patterns_multiset_limits(lp):
+    big = np.zeros((6, 13), dtype=np.complex128)      # C(18, 6) = 18564 > 6000
+    with pytest.raises(lp.LibpermError):
+        lp.patterns_multiset(big)
