@@ -115,8 +115,8 @@ class Clocks:
 # DRAM bytes (read + write) per n = 20 complex matrix of sz_batched_c128, from the ncu capture
 # summarised in profiles/sz_batched_c128_n20.md (304 matrices: 29.748599 GB + 7.624131 GB).
 # Valid only for the kernel source it was measured on; otherwise the bench reports null.
-TRAFFIC_C128_PER_MATRIX = (29.748599e9 + 7.624131e9) / 304
-TRAFFIC_SOURCE_SHA256 = "e5e105079b297ec54a6ae5fcbd85b18a1a9d7fb4789be24400718de97a8aa00f"
+TRAFFIC_C128_PER_MATRIX = (29.755192e9 + 7.625324e9) / 304
+TRAFFIC_SOURCE_SHA256 = "237762c6d4437af68d2bf0cf8da3525c09c5aa2e8e11d82fdf97af5bfe4a08ae"
 
 
 def traffic_per_launch(count: int):
