@@ -52,8 +52,10 @@
  * CUDA failures map to PERM_ECUDA.  Per-matrix conditions go to item_status.
  * No function aborts the process.
  *
- * Thread safety: a plan may be used by one host thread at a time; different
- * plans are independent.
+ * Thread safety: a plan may be used by one host thread at a time, and the work
+ * of two calls on one plan must not overlap on the GPU (they share the plan's
+ * workspace): use one stream per plan, or one plan per stream.  Different plans
+ * are independent.
  */
 #ifndef LIBPERM_H
 #define LIBPERM_H

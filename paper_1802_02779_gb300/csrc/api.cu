@@ -127,8 +127,13 @@ perm_status plan_create_impl(int n_max, perm_dtype dtype, const perm_opts* opts,
                              size_t ext_ws_bytes, perm_plan_t* out);
 static perm_status plan_create_tuned(int n_max, perm_dtype dtype, const perm_opts* opts,
                                      perm_plan_t* out);
+// Kernel-shape choices of the autotuner (0 = default).
+struct PlanShape {
+    int m_low = 0;      // chain width of the batched kernel
+    int threads = 0;    // CTA size of the batched kernel
+};
 static perm_status plan_create_core(int n_max, perm_dtype dtype, const perm_opts* opts, void* ext_ws,
-                                    size_t ext_ws_bytes, int threads, perm_plan_t* out);
+                                    size_t ext_ws_bytes, PlanShape shape, perm_plan_t* out);
 
 extern "C" {
 
@@ -158,11 +163,11 @@ perm_status perm_plan_create(int n_max, perm_dtype dtype, const perm_opts* opts,
 
 perm_status plan_create_impl(int n_max, perm_dtype dtype, const perm_opts* opts, void* ext_ws,
                              size_t ext_ws_bytes, perm_plan_t* out) {
-    return plan_create_core(n_max, dtype, opts, ext_ws, ext_ws_bytes, 0, out);
+    return plan_create_core(n_max, dtype, opts, ext_ws, ext_ws_bytes, PlanShape{}, out);
 }
 
 static perm_status plan_create_core(int n_max, perm_dtype dtype, const perm_opts* opts, void* ext_ws,
-                                    size_t ext_ws_bytes, int threads, perm_plan_t* out) {
+                                    size_t ext_ws_bytes, PlanShape shape, perm_plan_t* out) {
     if (!out) return PERM_EINVAL;
     *out = nullptr;
     if (n_max < 0 || n_max > kMaxN || !valid_dtype(dtype)) return PERM_EINVAL;
@@ -185,13 +190,9 @@ static perm_status plan_create_core(int n_max, perm_dtype dtype, const perm_opts
     // experiment knobs (results are bit-identical for every choice)
     if (const char* v = getenv("LIBPERM_SZ_LOW")) { int x = atoi(v); if (x >= 1 && x <= kMaxLow) p->m_low = x; }
     if (const char* v = getenv("LIBPERM_SZ_THREADS")) { int x = atoi(v); if (sz_c128_threads_valid(x)) p->c128_threads = x; }
-    if (threads < 0) {               // tuned: -(m_low * 1000 + threads)
-        const int code = -threads;
-        p->m_low = code / 1000;
-        threads = code % 1000;
-    }
-    if (threads && dtype == PERM_C128 && sz_c128_threads_valid(threads)) p->c128_threads = threads;
-    if (threads && dtype != PERM_C128 && sz_int_threads_valid(threads)) p->int_threads = threads;
+    if (shape.m_low >= 1 && shape.m_low <= kMaxLow) p->m_low = shape.m_low;
+    if (dtype == PERM_C128 && sz_c128_threads_valid(shape.threads)) p->c128_threads = shape.threads;
+    if (dtype != PERM_C128 && sz_int_threads_valid(shape.threads)) p->int_threads = shape.threads;
     cudaError_t e = cudaGetDevice(&p->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
     size_t free_b = 0, total_b = 0;
@@ -592,11 +593,13 @@ float time_candidate(int n, perm_dtype dtype, const perm_opts& base, int threads
                      const void* d_mats, int count, void* d_out, cudaStream_t st) {
     perm_opts o = base;
     o.flags &= ~(PERM_FLAG_AUTOTUNE | PERM_FLAG_GRAPH | PERM_FLAG_PLAIN);
-    o.low_cols = m;
     o.max_batch = count;
     o.method = PERM_METHOD_SZ;
     perm_plan_t p = nullptr;
-    if (plan_create_core(n, dtype, &o, nullptr, 0, threads, &p) != PERM_OK) return -1.f;
+    PlanShape shape;
+    shape.m_low = m;
+    shape.threads = threads;
+    if (plan_create_core(n, dtype, &o, nullptr, 0, shape, &p) != PERM_OK) return -1.f;
     std::vector<int> sizes(count, n);
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
@@ -670,8 +673,12 @@ static perm_status plan_create_tuned(int n_max, perm_dtype dtype, const perm_opt
     }
     // the tuned chain width applies to the batched path; the one-matrix path keeps its own
     perm_plan_t p = nullptr;
-    const int code = best.ms > 0.f ? -(best.m_low * 1000 + best.threads) : 0;
-    perm_status s = plan_create_core(n_max, dtype, &o, nullptr, 0, code, &p);
+    PlanShape shape;
+    if (best.ms > 0.f) {
+        shape.m_low = best.m_low;
+        shape.threads = best.threads;
+    }
+    perm_status s = plan_create_core(n_max, dtype, &o, nullptr, 0, shape, &p);
     if (s != PERM_OK) return s;
     if (p) p->tuned = best.ms > 0.f;
     *out = p;
