@@ -338,14 +338,18 @@ def run_gpu(args, rank, world):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64+u64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": N, "complex128": count, "zero_one": count,
-                       "method": "Store-zechin, persistent batched launch (one CTA per matrix)",
+                       "method": {"complex128": "Store-zechin, persistent batched launch (one CTA per matrix)",
+                                  "zero_one": "Ryser Gray-code kernel (PERM_METHOD_AUTO's method for integers): "
+                                              "width kernel, one CTA per 2^17 codes, finishing kernel"},
                        "l2": "flushed between timed steps (256 MB write)",
                        "plans": {"complex128": pc.describe(), "zero_one": pi.describe()},
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "complex_perm_per_s": count / (c_kernel_ms / 1000.0),
             "zero_one_perm_per_s": count / (float(np.mean(i_ms)) / 1000.0),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": 2 * args.steps, "clocks": ck}
+            # per step: the batched Store-zechin kernel (complex) and the Ryser width, Gray-code
+            # and finishing kernels (0/1, all 4096 matrices in one group)
+            "gpu_launches": 4 * args.steps, "clocks": ck}
     line.update(extras)
     print(json.dumps(line), flush=True)
     if dist:
@@ -392,10 +396,62 @@ def measure_extras(lp, torch, cm, im, stream, c_kernel_ms, count):
             res[name + "_value"] = [float(o32[0].real), float(o32[0].imag)]
     res["sz_fp64_tflops"] = sz_c128_flops(32) / (res["store_zechin_ms"] / 1000.0) / 1e12
     out["n32"] = res
+    out["integer_methods"] = measure_integer_methods(lp, torch, im, stream, count)
+    out["wide"] = measure_wide(lp, torch, stream)
     out["five_boson"] = measure_five_boson(lp, torch, stream)
     out["uneven"] = measure_uneven(lp, torch, stream)
     out["serving"] = measure_serving(lp)
     return out
+
+
+def _event_ms(torch, stream, fn):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def measure_integer_methods(lp, torch, im, stream, count):
+    """The 4096 0/1 matrices of the workload through a Store-zechin plan and through
+    the default (Ryser) plan: permanents/s of each, results compared exactly."""
+    di = torch.from_numpy(np.ascontiguousarray(im).reshape(-1)).cuda()
+    res = {}
+    outs = {}
+    for name, meth in (("store_zechin", lp.METHOD_SZ), ("ryser", lp.METHOD_AUTO)):
+        o = torch.empty((count, 2), dtype=torch.int64, device="cuda")
+        with lp.Plan(N, "u01", method=meth, max_batch=count) as p:
+            p.batch(di, [N] * count, o, None, stream)
+            torch.cuda.synchronize()
+            ms = _event_ms(torch, stream, lambda: p.batch(di, [N] * count, o, None, stream))
+        res[name + "_perm_per_s"] = count / (ms / 1000.0)
+        outs[name] = o.cpu().numpy()
+    res["identical"] = bool(np.array_equal(outs["store_zechin"], outs["ryser"]))
+    return res
+
+
+def measure_wide(lp, torch, stream):
+    """Exact 0/1 permanents above 2^128 (PERM_FLAG_WIDE, Ryser modulo 2^192): one dense
+    36 x 36 matrix with 14 zeros (the GPU tests check such matrices against the
+    rook-number closed form)."""
+    n = 36
+    g = np.random.default_rng(3636)
+    cells = set()
+    while len(cells) < 14:
+        cells.add((int(g.integers(n)), int(g.integers(n))))
+    a = np.ones((n, n), dtype=np.int64)
+    for i, j in cells:
+        a[i, j] = 0
+    d = torch.from_numpy(a.reshape(-1)).cuda()
+    o = torch.empty(4, dtype=torch.int64, device="cuda")
+    with lp.Plan(n, "u01", max_batch=1, flags=lp.FLAG_WIDE) as p:
+        p.batch(d, [n], o, None, stream)
+        torch.cuda.synchronize()
+        ms = _event_ms(torch, stream, lambda: p.batch(d, [n], o, None, stream))
+    value = lp.words_to_int(o.cpu().numpy())
+    return {"n": n, "zeros": len(cells), "ms": ms, "bits": value.bit_length(),
+            "codes_per_s": 2.0 ** n / (ms / 1000.0), "value": str(value)}
 
 
 def measure_five_boson(lp, torch, stream, reps=20):

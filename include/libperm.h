@@ -15,6 +15,10 @@
  *  - Ryser's inclusion-exclusion formula (Section 3.3, Eqs. (2)-(4)) walked in
  *    Gray-code order.  It needs no tables and is the fallback when the
  *    Store-zechin tables do not fit the memory budget (and for n > 34).
+ *    For integer matrices it is also the default (PERM_METHOD_AUTO): on a
+ *    GB300 its register-resident walk is faster than the integer tables at
+ *    every order measured (n = 2..30), while for complex matrices Store-zechin
+ *    is faster from n = 10 on.
  *
  * Element types
  *   PERM_C128  complex128 entries, row-major, interleaved (re, im) doubles --
@@ -22,11 +26,12 @@
  *              IEEE binary64 (no reduced precision anywhere); the last sum of
  *              each method is compensated (double-double).
  *   PERM_U01   0/1 entries stored as int64.  Exact: computed modulo 2^64 or
- *              2^128, the width chosen per matrix from an upper bound on
- *              per(A) (min of the products of row sums and of column sums, and
- *              Bregman's bound), so the result is the exact permanent.
- *   PERM_I64   small nonnegative integer entries stored as int64.  Exact as
- *              above (row/column-sum bound).
+ *              2^128 (or 2^192 with PERM_FLAG_WIDE), the width chosen per
+ *              matrix from an upper bound on per(A) (min of the products of
+ *              row sums and of column sums, and Bregman's bound), so the result
+ *              is the exact permanent.
+ *   PERM_I64   small nonnegative integer entries (each at most 2^40) stored as
+ *              int64.  Exact as above (row/column-sum bound).
  *
  * Conventions
  *   - Matrices of one call are concatenated: matrix i starts at element
@@ -36,11 +41,14 @@
  *   - n = 0 is allowed and gives per = 1 (empty product).  1 <= n <= 34 may use
  *     Store-zechin; Ryser accepts n <= 40 (complex) and n <= 40 (integers).
  *   - Results: PERM_C128 -> double2 out[count] (re, im).  Integer types ->
- *     uint64 out[2*count], (low, high) words of a 128-bit unsigned value.
+ *     uint64 out[2*count], (low, high) words of a 128-bit unsigned value; with
+ *     PERM_FLAG_WIDE uint64 out[4*count], the four words of a 256-bit unsigned
+ *     value, least significant first (the fourth is always zero).
  *   - `item_status` (optional, device int[count]) receives PERM_OK, or
- *     PERM_EOVERFLOW when the bound exceeds 2^128 (the result is then per(A)
- *     mod 2^128), or PERM_EINVAL for an entry that is negative (or not 0/1 for
- *     PERM_U01).
+ *     PERM_EOVERFLOW when the bound reaches 2^128 (2^192 with PERM_FLAG_WIDE
+ *     and Ryser; the result is then per(A) modulo that power of two), or
+ *     PERM_EINVAL for an entry that is negative, above 2^40, or not 0/1 for
+ *     PERM_U01.
  *
  * Ownership: the caller owns every input and output buffer; the library owns
  * its workspace (Store-zechin tables, Ryser partial sums, item descriptors),
@@ -71,7 +79,7 @@ typedef enum perm_status {
     PERM_OK = 0,
     PERM_EINVAL = 1,      /* bad argument (size, pointer, dtype, method) */
     PERM_ENOMEM = 2,      /* workspace does not fit the budget or the device */
-    PERM_EOVERFLOW = 3,   /* integer bound >= 2^128 (per-item status) */
+    PERM_EOVERFLOW = 3,   /* integer bound >= 2^128, or 2^192 with PERM_FLAG_WIDE (per-item status) */
     PERM_ECUDA = 4,       /* a CUDA runtime call failed */
     PERM_EAGAIN = 5,      /* try again: queue full (submit) or not done (poll) */
     PERM_ETIMEDOUT = 6,   /* a bounded wait gave up */
@@ -86,7 +94,8 @@ typedef enum perm_dtype {
 } perm_dtype;
 
 typedef enum perm_method {
-    PERM_METHOD_AUTO = 0,   /* Store-zechin when its tables fit, else Ryser */
+    PERM_METHOD_AUTO = 0,   /* complex: Store-zechin when its tables fit, else Ryser;
+                               integers: Ryser (the faster method on GB300) */
     PERM_METHOD_SZ = 1,     /* Store-zechin only (PERM_ENOMEM if it cannot fit) */
     PERM_METHOD_RYSER = 2   /* Ryser / Gray code only */
 } perm_method;
@@ -103,6 +112,12 @@ typedef enum perm_method {
                                  batched Store-zechin kernel on a synthetic batch and keep the
                                  fastest (results are bit-identical for every choice); cached
                                  per process and in the file LIBPERM_TUNE_CACHE names, if set */
+#define PERM_FLAG_WIDE 8u     /* integer plans only (PERM_EINVAL for PERM_C128): results are
+                                 256-bit slots (four uint64 per matrix), and Ryser computes
+                                 modulo 2^192, so every permanent whose bound is below 2^192 is
+                                 exact -- all 0/1 matrices up to n = 40 (40! < 2^160).
+                                 Store-zechin (PERM_METHOD_SZ) stays at most 128 bits wide and
+                                 reports PERM_EOVERFLOW above that */
 
 typedef struct perm_opts {
     size_t mem_budget_bytes;  /* workspace cap; 0 = 45% of the free device memory */
@@ -138,7 +153,8 @@ int perm_plan_describe(perm_plan_t plan, char *buf, size_t len);
    NULL = the legacy default stream).
      mats        device pointer, concatenated row-major matrices (see above)
      sizes       HOST int[count], each in [0, n_max]
-     out         device pointer, double2[count] or uint64[2*count]
+     out         device pointer, double2[count], uint64[2*count], or uint64[4*count]
+                 with PERM_FLAG_WIDE
      item_status device int[count] or NULL
    The call returns once the work is enqueued.  Inputs must stay valid and
    unmodified until the stream reaches that point. */
@@ -159,19 +175,23 @@ perm_status perm_batch_host(perm_plan_t plan, const void *mats, const int *sizes
      perm_submit copies the host matrix (n*n elements of `dtype`) and returns a
        ticket; PERM_EAGAIN if the queue is full.
      perm_poll returns PERM_EAGAIN until the ticket is done, then writes the 16
-       result bytes (double2, or (low, high) uint64) and the item status.
+       result bytes (double2, or (low, high) uint64) and the item status; a
+       server created with PERM_FLAG_WIDE writes 32 bytes for integer requests
+       (four uint64, as perm_batch with that flag).
      perm_server_destroy stops the server; PERM_ETIMEDOUT if in-flight work
        does not finish within timeout_ms (the server is then left to drain in
-       the background and its memory is not freed).
+       the background and its memory is not freed; at process exit its worker
+       thread is stopped and joined before the CUDA runtime shuts down).
    Server options: mem_budget_bytes = Store-zechin table budget of the large
    lane (0 = min(80 GB, a third of the free memory)); max_batch = queue
-   capacity (0 = 65536); the other fields are ignored.  Orders n <= 20 are
-   batched together; larger orders run one at a time, with Store-zechin when
-   their tables fit the budget and with Ryser otherwise. */
+   capacity (0 = 65536); flags: PERM_FLAG_WIDE as for plans; the other fields
+   are ignored.  Orders n <= 20 are batched together; larger complex orders run
+   one at a time, with Store-zechin when their tables fit the budget and with
+   Ryser otherwise; larger integer orders run with Ryser. */
 perm_status perm_server_create(const perm_opts *opts, void *stream, perm_server_t *out);
 perm_status perm_submit(perm_server_t server, const void *host_mat, int n, perm_dtype dtype,
                         uint64_t *ticket);
-perm_status perm_poll(perm_server_t server, uint64_t ticket, void *out16, int *item_status);
+perm_status perm_poll(perm_server_t server, uint64_t ticket, void *out, int *item_status);
 perm_status perm_server_destroy(perm_server_t server, int timeout_ms);
 
 /* Amplitudes of all collision-free output patterns of boson-sampling inputs in

@@ -9,6 +9,8 @@
 //                        workspace fits one CTA slice (one CTA per matrix),
 //                        larger ones one at a time over the whole GPU
 //   - Ryser           -> one launch per distinct order (plus a finishing kernel)
+// PERM_METHOD_AUTO sends complex matrices to Store-zechin where its tables
+// fit and integer matrices to Ryser (auto_uses_sz, with the measurements).
 // The method per matrix depends only on (n, dtype) and the plan, so a matrix
 // gives bit-identical results alone or in any batch.
 #include "perm_internal.cuh"
@@ -59,6 +61,7 @@ struct perm_plan_s {
     int m_single = 13;            // chain width of the one-matrix-over-the-GPU path
     int c128_threads = 384;       // CTA size of the batched complex kernel
     int int_threads = 256;        // CTA size of the batched integer kernel
+    int out_words = 2;            // integer result slot in 64-bit words (4 with PERM_FLAG_WIDE)
     size_t budget = 0;
 
     // Store-zechin
@@ -142,7 +145,7 @@ const char* perm_strerror(perm_status s) {
         case PERM_OK: return "ok";
         case PERM_EINVAL: return "invalid argument";
         case PERM_ENOMEM: return "workspace does not fit the memory budget";
-        case PERM_EOVERFLOW: return "integer permanent bound exceeds 2^128";
+        case PERM_EOVERFLOW: return "integer permanent bound exceeds the result width (2^128; 2^192 with PERM_FLAG_WIDE)";
         case PERM_ECUDA: return "CUDA runtime error";
         case PERM_EAGAIN: return "try again";
         case PERM_ETIMEDOUT: return "timed out";
@@ -177,6 +180,7 @@ static perm_status plan_create_core(int n_max, perm_dtype dtype, const perm_opts
     if (o.max_batch < 0 || o.ctas_per_sm < 0 || o.low_cols < 0 || o.low_cols > kMaxLow)
         return PERM_EINVAL;
     if (o.method == PERM_METHOD_SZ && n_max > kMaxNSZ) return PERM_EINVAL;
+    if ((o.flags & PERM_FLAG_WIDE) && dtype == PERM_C128) return PERM_EINVAL;
 
     perm_plan_t p = new (std::nothrow) perm_plan_s();
     if (!p) return PERM_ENOMEM;
@@ -184,6 +188,7 @@ static perm_status plan_create_core(int n_max, perm_dtype dtype, const perm_opts
     p->dtype = dtype;
     p->method = o.method;
     p->flags = o.flags;
+    p->out_words = (o.flags & PERM_FLAG_WIDE) ? 4 : 2;
     p->max_batch = o.max_batch ? o.max_batch : 65536;
     p->m_low = o.low_cols ? o.low_cols : 12;
     p->m_single = o.low_cols ? o.low_cols : 13;
@@ -203,7 +208,8 @@ static perm_status plan_create_core(int n_max, perm_dtype dtype, const perm_opts
 
     // ---- Store-zechin workspace ----
     size_t sz_batched = 0, sz_single = 0;
-    if (p->method != PERM_METHOD_RYSER && n_max >= 1) {
+    const bool uses_sz = p->method == PERM_METHOD_SZ || (p->method == PERM_METHOD_AUTO && auto_uses_sz(dtype));
+    if (uses_sz && n_max >= 1) {
         p->sz_batch_nmax = sz_batch_limit(p);
         p->sz_ws_per_cta = sz_matrix_workspace_bytes(dtype, p->sz_batch_nmax, p->m_low);
         if (sz_init_tables() != cudaSuccess) { delete p; return PERM_ECUDA; }
@@ -230,13 +236,13 @@ static perm_status plan_create_core(int n_max, perm_dtype dtype, const perm_opts
     }
     p->ws_bytes = std::max(sz_batched, sz_single);
 
-    // ---- Ryser partials: enough for max_batch matrices of order <= 25 or one big matrix ----
-    long long cap = 0;
-    for (int n = 1; n <= n_max; n++) {
-        long long parts = ryser_parts(dtype, n);
-        cap = std::max(cap, parts);
-    }
-    cap = std::max<long long>(cap, (long long)p->max_batch);
+    // ---- Ryser partials (32 B per piece of 2^17 codes): one matrix of the largest order,
+    // max_batch matrices of one piece each, and up to 2^20 pieces (32 MB) so that a batch of
+    // mid-size matrices fills the GPU in one launch instead of many small ones ----
+    long long max_parts = 1;
+    for (int n = 1; n <= n_max; n++) max_parts = std::max(max_parts, ryser_parts(dtype, n));
+    long long cap = std::max<long long>(max_parts, (long long)p->max_batch);
+    cap = std::max<long long>(cap, std::min<long long>(max_parts * (long long)p->max_batch, 1ll << 20));
     p->partials_cap = cap;
     p->partials_bytes = (size_t)cap * 32;
 
@@ -296,10 +302,10 @@ int perm_plan_describe(perm_plan_t p, char* buf, size_t len) {
                     "{\"dtype\": \"%s\", \"n_max\": %d, \"method\": %d, \"flags\": %u, "
                     "\"sz_batch_nmax\": %d, \"sz_single_nmax\": %d, \"chain_width_batched\": %d, "
                     "\"chain_width_single\": %d, \"cta_threads\": %d, \"batched_grid\": %d, "
-                    "\"workspace_bytes\": %zu, \"autotuned\": %s}",
+                    "\"workspace_bytes\": %zu, \"out_words\": %d, \"autotuned\": %s}",
                     dt, p->n_max, p->method, p->flags, p->sz_batch_nmax, p->sz_single_nmax, p->m_low,
                     p->m_single, p->dtype == PERM_C128 ? p->c128_threads : p->int_threads, p->sz_grid,
-                    perm_plan_workspace_bytes(p),
+                    perm_plan_workspace_bytes(p), p->dtype == PERM_C128 ? 0 : p->out_words,
                     p->tuned ? "true" : "false");
 }
 
@@ -337,7 +343,7 @@ perm_status classify(perm_plan_t p, const int* sizes, int count, BatchLayout& L)
             if (n > p->sz_single_nmax) return PERM_ENOMEM;
             use_sz = true;
         } else if (p->method == PERM_METHOD_AUTO) {
-            use_sz = n <= p->sz_single_nmax;
+            use_sz = auto_uses_sz(p->dtype) && n <= p->sz_single_nmax;
         }
         if (use_sz) {
             if (!plain && n <= p->sz_batch_nmax) szb.push_back(d);
@@ -368,7 +374,7 @@ perm_status enqueue(perm_plan_t p, const BatchLayout& L, const void* mats, const
     const bool plain = (p->flags & PERM_FLAG_PLAIN) != 0;
     cudaError_t e;
     if (L.ntriv) {
-        e = launch_trivial(p->dtype, dd + L.triv_at, (int)L.ntriv, out, item_status, st);
+        e = launch_trivial(p->dtype, dd + L.triv_at, (int)L.ntriv, out, p->out_words, item_status, st);
         if (e != cudaSuccess) return PERM_ECUDA;
     }
     if (L.nszb) {
@@ -376,16 +382,16 @@ perm_status enqueue(perm_plan_t p, const BatchLayout& L, const void* mats, const
         if (e != cudaSuccess) return PERM_ECUDA;
         const int grid = std::min<int>(p->sz_grid, (int)L.nszb);
         e = sz_launch_batched(p->dtype, mats, dd + L.szb_at, (int)L.nszb, L.szb_nmax, p->m_low,
-                              p->dtype == PERM_C128 ? p->c128_threads : p->int_threads, out, item_status,
-                              p->ws, p->sz_ws_per_cta, grid, p->d_counter, st);
+                              p->dtype == PERM_C128 ? p->c128_threads : p->int_threads, out, p->out_words,
+                              item_status, p->ws, p->sz_ws_per_cta, grid, p->d_counter, st);
         if (e != cudaSuccess) return PERM_ECUDA;
     }
     for (auto& d : L.szs) {
         // two CTAs' worth of chains per SM and layer: the per-CTA set-up is amortised, and
         // every layer is its own launch, which gives the scheduler a point to interleave
         // work from higher-priority streams
-        e = sz_launch_single(p->dtype, mats, d.offset, d.n, p->m_single, d.out_index, out, item_status,
-                             p->ws, 2 * p->num_sms, st);
+        e = sz_launch_single(p->dtype, mats, d.offset, d.n, p->m_single, d.out_index, out, p->out_words,
+                             item_status, p->ws, 2 * p->num_sms, st);
         if (e != cudaSuccess) return PERM_ECUDA;
     }
     for (auto& g : L.ry) {
@@ -396,7 +402,7 @@ perm_status enqueue(perm_plan_t p, const BatchLayout& L, const void* mats, const
         for (int b0 = 0; b0 < g.cnt; b0 += (int)per_launch) {
             const int c = (int)std::min<long long>(per_launch, g.cnt - b0);
             e = ryser_launch_group(p->dtype, g.n, mats, dd + g.at + b0, c, p->partials, p->d_widths,
-                                   out, item_status, 1 << 30, st);
+                                   out, p->out_words, p->out_words == 4, item_status, 1 << 30, st);
             if (e != cudaSuccess) return PERM_ECUDA;
         }
     }
@@ -521,8 +527,9 @@ perm_status perm_batch_host(perm_plan_t p, const void* mats, const int* sizes, i
         if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? PERM_ENOMEM : PERM_ECUDA;
         p->d_in_bytes = in_bytes;
     }
+    const size_t out_bytes = p->dtype == PERM_C128 ? 16 : 8 * (size_t)p->out_words;
     if (!p->d_out) {
-        e = cudaMalloc(&p->d_out, (size_t)p->max_batch * 16);
+        e = cudaMalloc(&p->d_out, (size_t)p->max_batch * out_bytes);
         if (e == cudaSuccess) e = cudaMalloc(&p->d_status, (size_t)p->max_batch * sizeof(int));
         if (e != cudaSuccess) return PERM_ECUDA;
     }
@@ -530,7 +537,7 @@ perm_status perm_batch_host(perm_plan_t p, const void* mats, const int* sizes, i
     if (e != cudaSuccess) return PERM_ECUDA;
     perm_status s = perm_batch(p, p->d_in, sizes, count, p->d_out, p->d_status, st);
     if (s != PERM_OK) return s;
-    e = cudaMemcpyAsync(out, p->d_out, (size_t)count * 16, cudaMemcpyDeviceToHost, st);
+    e = cudaMemcpyAsync(out, p->d_out, (size_t)count * out_bytes, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess && item_status)
         e = cudaMemcpyAsync(item_status, p->d_status, (size_t)count * sizeof(int),
                             cudaMemcpyDeviceToHost, st);
@@ -592,7 +599,7 @@ void tune_cache_store(int dev, int dtype, int n, const TuneChoice& c) {
 float time_candidate(int n, perm_dtype dtype, const perm_opts& base, int threads, int m,
                      const void* d_mats, int count, void* d_out, cudaStream_t st) {
     perm_opts o = base;
-    o.flags &= ~(PERM_FLAG_AUTOTUNE | PERM_FLAG_GRAPH | PERM_FLAG_PLAIN);
+    o.flags &= ~(PERM_FLAG_AUTOTUNE | PERM_FLAG_GRAPH | PERM_FLAG_PLAIN | PERM_FLAG_WIDE);
     o.max_batch = count;
     o.method = PERM_METHOD_SZ;
     perm_plan_t p = nullptr;
@@ -632,7 +639,8 @@ static perm_status plan_create_tuned(int n_max, perm_dtype dtype, const perm_opt
     // the order the batched kernel is tuned at: the plan's largest batched order, at most 20
     const int n = std::min(n_max, 20);
     TuneChoice best{0, 0, 0.f};
-    if (o.method != PERM_METHOD_RYSER && n >= 14 && !o.low_cols && !o.ctas_per_sm &&
+    const bool uses_sz = o.method == PERM_METHOD_SZ || (o.method == PERM_METHOD_AUTO && auto_uses_sz(dtype));
+    if (uses_sz && n >= 14 && !o.low_cols && !o.ctas_per_sm &&
         !tune_cache_lookup(dev, dtype, n, &best)) {
         const int count = 4 * sms;
         const size_t eb = dtype == PERM_C128 ? 16 : 8;

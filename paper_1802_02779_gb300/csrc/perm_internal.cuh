@@ -73,10 +73,10 @@ __device__ __forceinline__ double dd_round(dd2 x) { return __dadd_rn(x.hi, x.lo)
 // Integer width decision (exactness of the modular arithmetic).
 // Store-zechin and Ryser are polynomial identities over the integers, so
 // evaluating them modulo 2^w yields per(A) mod 2^w, which equals per(A) when
-// 0 <= per(A) < 2^w.  The width is the smallest of 64/128 that an upper bound
-// on per(A) allows.
+// 0 <= per(A) < 2^w.  The width is the smallest of 64/128 (and 192 where the
+// caller allows it) that an upper bound on per(A) allows.
 // ---------------------------------------------------------------------------
-enum : int { kWidth64 = 64, kWidth128 = 128, kWidthOverflow = 0, kWidthInvalid = -1 };
+enum : int { kWidth64 = 64, kWidth128 = 128, kWidth192 = 192, kWidthOverflow = 0, kWidthInvalid = -1 };
 
 // Saturating 128-bit product (saturates at 2^128 - 1).
 __device__ __forceinline__ unsigned __int128 sat_mul128(unsigned __int128 a, unsigned long long b) {
@@ -90,11 +90,13 @@ __device__ __forceinline__ unsigned __int128 sat_mul128(unsigned __int128 a, uns
 // the entries: negative -> invalid; for 0/1 input, anything else -> invalid.
 // Bounds: per(A) <= prod_i r_i and <= prod_j c_j (row/column sums); for 0/1
 // matrices also Bregman's bound per(A) <= prod_i (r_i!)^(1/r_i) (Bregman,
-// Soviet Math. Dokl. 14 (1973)), evaluated in log2 with a 0.01-bit margin.
-// Executed by one thread.
-__device__ inline int decide_width(const long long* a, int n, bool zero_one) {
+// Soviet Math. Dokl. 14 (1973)).  The 64- and 128-bit tests on the products
+// are exact; the Bregman test and the 192-bit test compare log2 of the bound
+// with a 0.01-bit margin (the rounding error of a sum of at most 80 log2
+// terms is below 1e-12 bits).  Executed by one thread.
+__device__ inline int decide_width(const long long* a, int n, bool zero_one, bool allow192 = false) {
     unsigned __int128 prow = 1, pcol = 1;
-    double breg = 0.0;
+    double breg = 0.0, lrow = 0.0, lcol = 0.0;
     for (int i = 0; i < n; i++) {
         unsigned long long rs = 0;
         for (int j = 0; j < n; j++) {
@@ -104,6 +106,7 @@ __device__ inline int decide_width(const long long* a, int n, bool zero_one) {
             rs += (unsigned long long)v;
         }
         prow = sat_mul128(prow, rs);
+        lrow += log2((double)rs);
         if (zero_one && rs > 1) {
             double lf = 0.0;
             for (unsigned long long q = 2; q <= rs; q++) lf += log2((double)q);
@@ -114,14 +117,19 @@ __device__ inline int decide_width(const long long* a, int n, bool zero_one) {
         unsigned long long cs = 0;
         for (int i = 0; i < n; i++) cs += (unsigned long long)a[(size_t)i * n + j];
         pcol = sat_mul128(pcol, cs);
+        lcol += log2((double)cs);
     }
     unsigned __int128 b = prow < pcol ? prow : pcol;
     const unsigned __int128 two64 = (unsigned __int128)1 << 64;
     const unsigned __int128 maxv = ~(unsigned __int128)0;
-    if (b < two64) return kWidth64;
+    if (b < two64) return kWidth64;      // also every matrix with a zero row or column
     if (zero_one && breg < 63.99) return kWidth64;
     if (b < maxv) return kWidth128;
     if (zero_one && breg < 127.99) return kWidth128;
+    if (allow192) {
+        const double lb = lrow < lcol ? lrow : lcol;
+        if (lb < 191.99 || (zero_one && breg < 191.99)) return kWidth192;
+    }
     return kWidthOverflow;
 }
 
@@ -145,28 +153,44 @@ int sz_c128_threads_valid(int threads);
 int sz_int_threads_valid(int threads);
 cudaError_t sz_init_tables();                              // once per device (idempotent)
 
+// Integer results are written as `out_words` 64-bit words per matrix (2: a
+// 128-bit slot; 4: a 256-bit slot, the words above the computed width zero).
+// Complex results are always one double2.
+
 // Batched: one CTA per matrix, persistent over `count` items (dynamic order by
 // an atomic counter at *counter, which must be zero at launch).
 cudaError_t sz_launch_batched(int dtype, const void* mats, const ItemDesc* items, int count,
-                              int n_max, int m, int threads, void* out, int* item_status,
-                              void* workspace, size_t ws_per_cta, int grid, unsigned* counter,
-                              cudaStream_t st);
+                              int n_max, int m, int threads, void* out, int out_words,
+                              int* item_status, void* workspace, size_t ws_per_cta, int grid,
+                              unsigned* counter, cudaStream_t st);
 
 // One matrix, all CTAs on the chains of one layer at a time (t+1 launches).
 cudaError_t sz_launch_single(int dtype, const void* mats, long long offset, int n, int m,
-                             int out_index, void* out, int* item_status, void* workspace,
-                             int grid_cap, cudaStream_t st);
+                             int out_index, void* out, int out_words, int* item_status,
+                             void* workspace, int grid_cap, cudaStream_t st);
 
 // Ryser: every matrix's codes are cut into ryser_parts(dtype, n) CTA-sized
-// pieces (a function of n only).  One launch per distinct order n.
+// pieces (a function of n only).  One launch per distinct order n.  allow192:
+// integer widths up to 192 bits (requires out_words = 4).
 long long ryser_parts(int dtype, int n);
 cudaError_t ryser_launch_group(int dtype, int n, const void* mats, const ItemDesc* items, int count,
-                               void* partials, int* widths, void* out, int* item_status, int grid,
-                               cudaStream_t st);
+                               void* partials, int* widths, void* out, int out_words, bool allow192,
+                               int* item_status, int grid, cudaStream_t st);
 
 // n = 0 items: per = 1.
-cudaError_t launch_trivial(int dtype, const ItemDesc* items, int count, void* out,
+cudaError_t launch_trivial(int dtype, const ItemDesc* items, int count, void* out, int out_words,
                            int* item_status, cudaStream_t st);
+
+// Method of PERM_METHOD_AUTO.  Measured on GB300 (batches of 1..4096 matrices,
+// n = 2..30): for integer inputs Ryser's register-resident Gray-code walk is
+// faster than the Store-zechin tables at every order (1.1x at n <= 12, about
+// 2x at n = 13..22, 3-12x at n >= 23, where the tables no longer fit one CTA's
+// slice and the one-matrix layer path runs), because integer Store-zechin does
+// one addition per table read and waits on memory; for complex inputs
+// Store-zechin is faster from n = 10 on (1.3-1.6x), and within 10% below.  So
+// AUTO evaluates complex matrices with Store-zechin where the tables fit and
+// integer matrices with Ryser.
+inline bool auto_uses_sz(int dtype) { return dtype == PERM_C128; }
 
 
 }  // namespace perm

@@ -2,8 +2,8 @@
 // arXiv:1802.02779, Section 3.3, Eqs. (2)-(4)), the memory-free fallback.
 //
 // Integers: Eq. (4),  per(A) = (-1)^n sum_{S subset cols} (-1)^{|S|} prod_i sum_{j in S} a_ij,
-// over all 2^n subsets, modulo 2^64 or 2^128 (exact under the bound chosen by
-// decide_width).  The subsets are visited in binary-reflected Gray-code order,
+// over all 2^n subsets, modulo 2^64, 2^128 or 2^192 (exact under the bound
+// chosen by decide_width).  The subsets are visited in binary-reflected Gray-code order,
 // so consecutive subsets differ in one column and each row sum is updated by
 // one addition (the reuse Section 3.3 asks for).
 //
@@ -26,6 +26,7 @@
 #include "perm_internal.cuh"
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 namespace perm {
@@ -44,7 +45,8 @@ __host__ __device__ inline long long parts_for(int dtype, int n) {
 }
 
 struct CPartial { double re_hi, re_lo, im_hi, im_lo; };
-struct IPartial { unsigned long long lo, hi, status, width; };
+// meta: item status in the low 32 bits, the width computed (0, 64, 128, 192) above
+struct IPartial { unsigned long long w0, w1, w2, meta; };
 
 // ---------------------------------------------------------------------------
 // Complex (Glynn), compile-time order N.
@@ -150,81 +152,201 @@ ryser_c128_kernel(const double2* __restrict__ mats, const ItemDesc* __restrict__
 }
 
 // ---------------------------------------------------------------------------
-// Integers (Eq. 4) modulo 2^64 / 2^128, compile-time order N.
+// Integers (Eq. 4) modulo 2^64, 2^128 or 2^192, compile-time order N.
+//
+// Row sums r_i(S) = sum_{j in S} a_ij are updated by one column per Gray step.
+// 0/1 input (ZO): r_i <= N <= 40, so the row sums are 32-bit and six of them
+// multiply exactly in 32 bits (40^6 < 2^32); the running product then takes
+// one 32-bit factor per group of six rows, limb by limb.  Other integers:
+// 64-bit row sums and factors, with two independent product chains (even and
+// odd rows) for instruction-level parallelism.  Every grouping is the same
+// product modulo 2^W, so results do not depend on it.
 // ---------------------------------------------------------------------------
 struct U128 { unsigned long long lo, hi; };
 
-__device__ __forceinline__ U128 u128_add(U128 a, U128 b) {
-    const unsigned long long lo = a.lo + b.lo;
-    return {lo, a.hi + b.hi + (lo < a.lo ? 1ull : 0ull)};
-}
-__device__ __forceinline__ U128 u128_sub(U128 a, U128 b) {
-    const unsigned long long lo = a.lo - b.lo;
-    return {lo, a.hi - b.hi - (a.lo < b.lo ? 1ull : 0ull)};
-}
 __device__ __forceinline__ U128 u128_mul_u64(U128 a, unsigned long long b) {
     return {a.lo * b, __umul64hi(a.lo, b) + a.hi * b};
 }
+__device__ __forceinline__ U128 u128_mul(U128 a, U128 b) {
+    return {a.lo * b.lo, __umul64hi(a.lo, b.lo) + a.lo * b.hi + a.hi * b.lo};
+}
 
-template <int N, bool W128>
-__device__ __forceinline__ void ryser_int_range(const long long (*s_col)[N > 0 ? N : 1],
-                                                unsigned long long g0, int log_len, U128& acc) {
-    // row sums of gray(g0) directly
+// acc += x / acc -= x over the low K words (K = 1, 2, 3), carries propagated.
+template <int K>
+__device__ __forceinline__ void words_add(unsigned long long (&acc)[3], const unsigned long long (&x)[3]) {
+    if constexpr (K == 1) {
+        acc[0] += x[0];
+    } else if constexpr (K == 2) {
+        asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, %3;"
+            : "+l"(acc[0]), "+l"(acc[1]) : "l"(x[0]), "l"(x[1]));
+    } else {
+        asm("add.cc.u64 %0, %0, %3;\n\taddc.cc.u64 %1, %1, %4;\n\taddc.u64 %2, %2, %5;"
+            : "+l"(acc[0]), "+l"(acc[1]), "+l"(acc[2]) : "l"(x[0]), "l"(x[1]), "l"(x[2]));
+    }
+}
+template <int K>
+__device__ __forceinline__ void words_sub(unsigned long long (&acc)[3], const unsigned long long (&x)[3]) {
+    if constexpr (K == 1) {
+        acc[0] -= x[0];
+    } else if constexpr (K == 2) {
+        asm("sub.cc.u64 %0, %0, %2;\n\tsubc.u64 %1, %1, %3;"
+            : "+l"(acc[0]), "+l"(acc[1]) : "l"(x[0]), "l"(x[1]));
+    } else {
+        asm("sub.cc.u64 %0, %0, %3;\n\tsubc.cc.u64 %1, %1, %4;\n\tsubc.u64 %2, %2, %5;"
+            : "+l"(acc[0]), "+l"(acc[1]), "+l"(acc[2]) : "l"(x[0]), "l"(x[1]), "l"(x[2]));
+    }
+}
+
+// p *= g modulo 2^(32 L), p in 32-bit limbs (least significant first).
+template <int L>
+__device__ __forceinline__ void limbs_mul_u32(unsigned (&p)[L], unsigned g) {
+    unsigned carry = 0;
+#pragma unroll
+    for (int k = 0; k < L - 1; k++) {
+        const unsigned long long t = (unsigned long long)p[k] * g + carry;   // < 2^64
+        p[k] = (unsigned)t;
+        carry = (unsigned)(t >> 32);
+    }
+    p[L - 1] = p[L - 1] * g + carry;
+}
+
+// prod_i r_i modulo 2^W into x[0..W/64-1].
+template <int N, int W>
+__device__ __forceinline__ void row_product(const unsigned (&r)[N], unsigned long long (&x)[3]) {
+    constexpr int kGroups = (N + 5) / 6;
+    unsigned g[kGroups];
+#pragma unroll
+    for (int q = 0; q < kGroups; q++) {
+        g[q] = r[6 * q];
+#pragma unroll
+        for (int i = 6 * q + 1; i < 6 * q + 6 && i < N; i++) g[q] *= r[i];
+    }
+    if constexpr (W == 64) {
+        unsigned long long p = g[0];
+#pragma unroll
+        for (int q = 1; q < kGroups; q++) p *= (unsigned long long)g[q];
+        x[0] = p;
+    } else {
+        constexpr int L = W / 32;
+        unsigned p[L];
+        p[0] = g[0];
+#pragma unroll
+        for (int k = 1; k < L; k++) p[k] = 0u;
+#pragma unroll
+        for (int q = 1; q < kGroups; q++) limbs_mul_u32<L>(p, g[q]);
+#pragma unroll
+        for (int k = 0; k < W / 64; k++) x[k] = (unsigned long long)p[2 * k] | ((unsigned long long)p[2 * k + 1] << 32);
+    }
+}
+template <int N, int W>
+__device__ __forceinline__ void row_product(const unsigned long long (&r)[N], unsigned long long (&x)[3]) {
+    if constexpr (N == 1) {
+        x[0] = r[0];
+        if constexpr (W >= 128) x[1] = 0ull;
+        if constexpr (W >= 192) x[2] = 0ull;
+    } else if constexpr (W == 64) {
+        unsigned long long pa = r[0], pb = r[1];
+#pragma unroll
+        for (int i = 2; i < N; i++) {
+            if (i & 1) pb *= r[i];
+            else pa *= r[i];
+        }
+        x[0] = pa * pb;
+    } else if constexpr (W == 128) {
+        U128 pa = {r[0], 0ull}, pb = {r[1], 0ull};
+#pragma unroll
+        for (int i = 2; i < N; i++) {
+            if (i & 1) pb = u128_mul_u64(pb, r[i]);
+            else pa = u128_mul_u64(pa, r[i]);
+        }
+        const U128 p = u128_mul(pa, pb);
+        x[0] = p.lo;
+        x[1] = p.hi;
+    } else {
+        unsigned long long w0 = r[0], w1 = 0ull, w2 = 0ull;
+#pragma unroll
+        for (int i = 1; i < N; i++) {
+            const unsigned long long b = r[i];
+            const unsigned long long h0 = __umul64hi(w0, b), h1 = __umul64hi(w1, b);
+            const unsigned long long t1 = w1 * b;
+            const unsigned long long n1 = t1 + h0;
+            w2 = w2 * b + h1 + (n1 < t1 ? 1ull : 0ull);
+            w1 = n1;
+            w0 = w0 * b;
+        }
+        x[0] = w0;
+        x[1] = w1;
+        x[2] = w2;
+    }
+}
+
+// One thread's contiguous range of 2^log_len Gray codes starting at code g0.
+// s_col: column j of A at s_col[j * NP .. j * NP + N - 1].
+template <int N, int NP, int W, typename E>
+__device__ __forceinline__ void ryser_int_range(const E* __restrict__ s_col, unsigned long long g0,
+                                                int log_len, unsigned long long (&acc)[3]) {
+    constexpr int K = W / 64;
     unsigned long long gr = g0 ^ (g0 >> 1);
-    long long r[N > 0 ? N : 1];
+    E r[N];
 #pragma unroll
     for (int i = 0; i < N; i++) r[i] = 0;
     for (int j = 0; j < N; j++) {
         if ((gr >> j) & 1ull) {
 #pragma unroll
-            for (int i = 0; i < N; i++) r[i] += s_col[j][i];
+            for (int i = 0; i < N; i++) r[i] += s_col[j * NP + i];
         }
     }
     // sign (-1)^(n - |S|)
     int neg = (N - __popcll(gr)) & 1;
     const unsigned long long len = 1ull << log_len;
-    U128 a = acc;
+    unsigned long long a[3] = {acc[0], acc[1], acc[2]};
     for (unsigned long long st = 0; st < len; st++) {
         if (st > 0) {
-            const int j = __ffsll((long long)st) - 1;
+            const int j = __ffsll((long long)st) - 1;   // the same column for the whole warp
             gr ^= 1ull << j;
+            const E* col = s_col + j * NP;
             if ((gr >> j) & 1ull) {
 #pragma unroll
-                for (int i = 0; i < N; i++) r[i] += s_col[j][i];
+                for (int i = 0; i < N; i++) r[i] += col[i];
             } else {
 #pragma unroll
-                for (int i = 0; i < N; i++) r[i] -= s_col[j][i];
+                for (int i = 0; i < N; i++) r[i] -= col[i];
             }
             neg ^= 1;
         }
-        if (W128) {
-            U128 p = {(unsigned long long)r[0], 0ull};
-#pragma unroll
-            for (int i = 1; i < N; i++) p = u128_mul_u64(p, (unsigned long long)r[i]);
-            a = neg ? u128_sub(a, p) : u128_add(a, p);
-        } else {
-            unsigned long long p = (unsigned long long)r[0];
-#pragma unroll
-            for (int i = 1; i < N; i++) p *= (unsigned long long)r[i];
-            a.lo = neg ? a.lo - p : a.lo + p;
-        }
+        unsigned long long x[3];
+        row_product<N, W>(r, x);
+        if (neg) words_sub<K>(a, x);
+        else words_add<K>(a, x);
     }
-    acc = a;
+    acc[0] = a[0];
+    acc[1] = a[1];
+    acc[2] = a[2];
 }
 
-template <int N>
+// Widest modulus an order-N matrix of the given kind can need: a 0/1 matrix
+// has per(A) <= n!, and 20! < 2^64, 34! < 2^128, 40! < 2^192.
+template <int N, bool ZO>
+constexpr int max_width() {
+    return !ZO ? 192 : (N <= 20 ? 64 : (N <= 34 ? 128 : 192));
+}
+
+template <int N, bool ZO>
 __global__ void __launch_bounds__(kRyserThreads)
 ryser_int_kernel(const long long* __restrict__ mats, const ItemDesc* __restrict__ items,
-                 long long total_parts, const int* __restrict__ widths,
+                 long long total_parts, const int* __restrict__ widths, int allow192,
                  IPartial* __restrict__ partials) {
-    __shared__ long long s_col[N > 0 ? N : 1][N > 0 ? N : 1];   // s_col[j][i] = a_ij
-    __shared__ U128 s_acc[kRyserThreads];
+    using E = typename std::conditional<ZO, unsigned, unsigned long long>::type;
+    constexpr int NP = ZO ? ((N + 3) & ~3) : ((N + 1) & ~1);   // 16-byte columns
+    __shared__ __align__(16) E s_col[N * NP];                   // s_col[j * NP + i] = a_ij
+    __shared__ unsigned long long s_acc[3][kRyserThreads];
     __shared__ int s_width;
     constexpr int G = N;
     constexpr long long kParts = (G > kLogCodesPerPart) ? (1ll << (G - kLogCodesPerPart)) : 1ll;
     constexpr int kLogPart = (G > kLogCodesPerPart) ? kLogCodesPerPart : G;
     constexpr int kLogThr = kLogPart >= 8 ? 8 : kLogPart;
     constexpr int kLogLen = kLogPart - kLogThr;
+    constexpr int kMaxW = max_width<N, ZO>();
 
     for (long long task = blockIdx.x; task < total_parts; task += gridDim.x) {
         const ItemDesc d = items[task / kParts];
@@ -233,30 +355,48 @@ ryser_int_kernel(const long long* __restrict__ mats, const ItemDesc* __restrict_
         __syncthreads();
         for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
             const int i = e / N, j = e % N;
-            s_col[j][i] = a[e];
+            s_col[j * NP + i] = (E)a[e];
         }
         if (threadIdx.x == 0) s_width = widths[task / kParts];
         __syncthreads();
         const int w = s_width;
-        U128 acc = {0ull, 0ull};
-        if (threadIdx.x < (1 << kLogThr)) {
+        // width computed: the decided one; past the bound, the widest the output holds
+        int cw = w == kWidthInvalid ? 0 : (w == kWidthOverflow ? (allow192 ? 192 : 128) : w);
+        if (cw > kMaxW) cw = kMaxW;
+        unsigned long long acc[3] = {0ull, 0ull, 0ull};
+        if (threadIdx.x < (1 << kLogThr) && cw > 0) {
             const unsigned long long g0 =
                 ((unsigned long long)part << kLogPart) + ((unsigned long long)threadIdx.x << kLogLen);
-            if (w == kWidth64) ryser_int_range<N, false>(s_col, g0, kLogLen, acc);
-            else ryser_int_range<N, true>(s_col, g0, kLogLen, acc);
+            if (cw == 64) ryser_int_range<N, NP, 64>(s_col, g0, kLogLen, acc);
+            if constexpr (kMaxW >= 128) {
+                if (cw == 128) ryser_int_range<N, NP, 128>(s_col, g0, kLogLen, acc);
+            }
+            if constexpr (kMaxW >= 192) {
+                if (cw == 192) ryser_int_range<N, NP, 192>(s_col, g0, kLogLen, acc);
+            }
         }
-        s_acc[threadIdx.x] = acc;
+        s_acc[0][threadIdx.x] = acc[0];
+        s_acc[1][threadIdx.x] = acc[1];
+        s_acc[2][threadIdx.x] = acc[2];
         __syncthreads();
         for (int h = kRyserThreads / 2; h > 0; h >>= 1) {
-            if (threadIdx.x < h) s_acc[threadIdx.x] = u128_add(s_acc[threadIdx.x], s_acc[threadIdx.x + h]);
+            if (threadIdx.x < h) {
+                unsigned long long x[3] = {s_acc[0][threadIdx.x + h], s_acc[1][threadIdx.x + h],
+                                           s_acc[2][threadIdx.x + h]};
+                unsigned long long y[3] = {s_acc[0][threadIdx.x], s_acc[1][threadIdx.x], s_acc[2][threadIdx.x]};
+                words_add<3>(y, x);
+                s_acc[0][threadIdx.x] = y[0];
+                s_acc[1][threadIdx.x] = y[1];
+                s_acc[2][threadIdx.x] = y[2];
+            }
             __syncthreads();
         }
         if (threadIdx.x == 0) {
             IPartial p;
-            p.lo = s_acc[0].lo;
-            p.hi = (w == kWidth64) ? 0ull : s_acc[0].hi;
-            p.status = (unsigned long long)width_status(w);
-            p.width = (unsigned long long)w;
+            p.w0 = s_acc[0][0];
+            p.w1 = s_acc[1][0];
+            p.w2 = s_acc[2][0];
+            p.meta = (unsigned long long)(unsigned)width_status(w) | ((unsigned long long)cw << 32);
             partials[task] = p;
         }
     }
@@ -294,49 +434,78 @@ __global__ void ryser_finish_c128(const ItemDesc* items, long long parts, int co
     }
 }
 
+// Sum the pieces of every integer matrix (one CTA of 128 threads per matrix;
+// modular addition is exact, so the order does not matter) and write the
+// out_words-word result: words above the computed width are zero.
 __global__ void ryser_finish_int(const ItemDesc* items, long long parts, int count,
-                                 const IPartial* partials, unsigned long long* out,
+                                 const IPartial* partials, unsigned long long* out, int out_words,
                                  int* item_status) {
-    const int it = blockIdx.x * blockDim.x + threadIdx.x;
+    const int it = blockIdx.x;
     if (it >= count) return;
-    U128 s = {0ull, 0ull};
-    int st = PERM_OK;
-    bool w64 = false;
-    for (long long p = (long long)it * parts; p < (long long)(it + 1) * parts; p++) {
-        s = u128_add(s, U128{partials[p].lo, partials[p].hi});
-        if (partials[p].status != PERM_OK) st = (int)partials[p].status;
-        w64 = partials[p].width == (unsigned long long)kWidth64;
+    __shared__ unsigned long long s[3][128];
+    unsigned long long acc[3] = {0ull, 0ull, 0ull};
+    const long long b = (long long)it * parts, e = b + parts;
+    for (long long p = b + threadIdx.x; p < e; p += blockDim.x) {
+        const unsigned long long x[3] = {partials[p].w0, partials[p].w1, partials[p].w2};
+        words_add<3>(acc, x);
     }
-    if (w64) s.hi = 0ull;       // the sum is only meaningful modulo 2^64
-    const int o = items[it].out_index;
-    out[2 * o] = s.lo;
-    out[2 * o + 1] = s.hi;
-    if (item_status) item_status[o] = st;
+    s[0][threadIdx.x] = acc[0];
+    s[1][threadIdx.x] = acc[1];
+    s[2][threadIdx.x] = acc[2];
+    __syncthreads();
+    for (int h = 64; h > 0; h >>= 1) {
+        if (threadIdx.x < h) {
+            unsigned long long y[3] = {s[0][threadIdx.x], s[1][threadIdx.x], s[2][threadIdx.x]};
+            const unsigned long long x[3] = {s[0][threadIdx.x + h], s[1][threadIdx.x + h], s[2][threadIdx.x + h]};
+            words_add<3>(y, x);
+            s[0][threadIdx.x] = y[0];
+            s[1][threadIdx.x] = y[1];
+            s[2][threadIdx.x] = y[2];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const unsigned long long meta = partials[b].meta;   // the same for every piece of the matrix
+        const int st = (int)(unsigned)(meta & 0xffffffffull);
+        const int cw = (int)(meta >> 32);
+        const int o = items[it].out_index;
+        unsigned long long* dst = out + (size_t)out_words * o;
+        dst[0] = cw >= 64 ? s[0][0] : 0ull;
+        dst[1] = cw >= 128 ? s[1][0] : 0ull;
+        if (out_words == 4) {
+            dst[2] = cw >= 192 ? s[2][0] : 0ull;
+            dst[3] = 0ull;
+        }
+        if (item_status) item_status[o] = st;
+    }
 }
 
 // Integer width of every matrix of a launch, once (one thread per matrix).
 __global__ void ryser_widths_kernel(const long long* mats, const ItemDesc* items, int count, int n,
-                                    int zero_one, int* widths) {
+                                    int zero_one, int allow192, int* widths) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < count) widths[i] = decide_width(mats + items[i].offset, n, zero_one != 0);
+    if (i < count) widths[i] = decide_width(mats + items[i].offset, n, zero_one != 0, allow192 != 0);
 }
 
 template <int N>
 cudaError_t launch_n(int dtype, const void* mats, const ItemDesc* items, long long total_parts,
-                     const int* widths, void* partials, int grid, cudaStream_t st) {
+                     const int* widths, int allow192, void* partials, int grid, cudaStream_t st) {
     const int g = (int)std::min<long long>(total_parts, (long long)grid);
     if (dtype == PERM_C128) {
         ryser_c128_kernel<N><<<g, kRyserThreads, 0, st>>>((const double2*)mats, items, total_parts,
                                                           (CPartial*)partials);
+    } else if (dtype == PERM_U01) {
+        ryser_int_kernel<N, true><<<g, kRyserThreads, 0, st>>>((const long long*)mats, items, total_parts,
+                                                               widths, allow192, (IPartial*)partials);
     } else {
-        ryser_int_kernel<N><<<g, kRyserThreads, 0, st>>>((const long long*)mats, items, total_parts,
-                                                         widths, (IPartial*)partials);
+        ryser_int_kernel<N, false><<<g, kRyserThreads, 0, st>>>((const long long*)mats, items, total_parts,
+                                                                widths, allow192, (IPartial*)partials);
     }
     return cudaGetLastError();
 }
 
-typedef cudaError_t (*launch_fn)(int, const void*, const ItemDesc*, long long, const int*, void*, int,
-                                 cudaStream_t);
+typedef cudaError_t (*launch_fn)(int, const void*, const ItemDesc*, long long, const int*, int, void*,
+                                 int, cudaStream_t);
 
 template <int... Ns>
 struct Table {
@@ -354,27 +523,29 @@ using NTable = Table<PERM_NS>;
 // `partials` holds count * ryser_parts(dtype, n) 32-byte slots and `widths`
 // count ints (integer types only).
 cudaError_t ryser_launch_group(int dtype, int n, const void* mats, const ItemDesc* items, int count,
-                               void* partials, int* widths, void* out, int* item_status, int grid,
-                               cudaStream_t st) {
+                               void* partials, int* widths, void* out, int out_words, bool allow192,
+                               int* item_status, int grid, cudaStream_t st) {
     if (count <= 0) return cudaSuccess;
     if (n < 1 || n > kMaxN) return cudaErrorInvalidValue;
+    if (dtype != PERM_C128 && out_words != 2 && out_words != 4) return cudaErrorInvalidValue;
+    if (allow192 && out_words != 4) return cudaErrorInvalidValue;
     const long long parts = parts_for(dtype, n);
     if (dtype != PERM_C128) {
         ryser_widths_kernel<<<(count + 127) / 128, 128, 0, st>>>((const long long*)mats, items, count, n,
-                                                                 dtype == PERM_U01, widths);
+                                                                 dtype == PERM_U01, allow192 ? 1 : 0,
+                                                                 widths);
         cudaError_t e0 = cudaGetLastError();
         if (e0 != cudaSuccess) return e0;
     }
-    cudaError_t e = NTable::fns[n - 1](dtype, mats, items, (long long)count * parts, widths, partials,
-                                       grid, st);
+    cudaError_t e = NTable::fns[n - 1](dtype, mats, items, (long long)count * parts, widths,
+                                       allow192 ? 1 : 0, partials, grid, st);
     if (e != cudaSuccess) return e;
     if (dtype == PERM_C128)
         ryser_finish_c128<<<count, 32, 0, st>>>(items, parts, count, (const CPartial*)partials,
                                                 (double2*)out, item_status);
     else
-        ryser_finish_int<<<(count + 127) / 128, 128, 0, st>>>(items, parts, count,
-                                                              (const IPartial*)partials,
-                                                              (unsigned long long*)out, item_status);
+        ryser_finish_int<<<count, 128, 0, st>>>(items, parts, count, (const IPartial*)partials,
+                                                (unsigned long long*)out, out_words, item_status);
     return cudaGetLastError();
 }
 

@@ -6,14 +6,16 @@
 //
 //   batch lane  orders n <= kSmallN: every pending request of this kind is
 //               taken into the next batch as soon as the previous batch of the
-//               lane has finished (continuous batching); Store-zechin with one
-//               CTA per matrix.  Highest stream priority.
-//   table lane  orders n > kSmallN whose Store-zechin chain tables (the
-//               "stored sub-permanents" of Section 4 of Su & Zheng,
+//               lane has finished (continuous batching); complex matrices by
+//               Store-zechin with one CTA per matrix, integers by Ryser.
+//               Highest stream priority.
+//   table lane  complex orders n > kSmallN whose Store-zechin chain tables
+//               (the "stored sub-permanents" of Section 4 of Su & Zheng,
 //               arXiv:1802.02779) fit the table budget: admitted one at a
 //               time into the budget.  Middle priority.
-//   Ryser lane  the other orders n > kSmallN: Ryser's formula (Section 3.3),
-//               which needs no tables.  Lowest priority.
+//   Ryser lane  the other orders n > kSmallN (and every larger integer
+//               order): Ryser's formula (Section 3.3), which needs no
+//               tables.  Lowest priority.
 //
 // The large lanes launch one CTA per chain or per piece of Gray codes, so
 // their CTAs retire every few milliseconds and a batch that arrives on the
@@ -26,6 +28,7 @@
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <memory>
@@ -53,7 +56,8 @@ struct Request {
     int dtype = PERM_C128;
     std::vector<unsigned char> mat;       // host copy of the input
     std::atomic<int> state{0};            // 0 queued, 1 on device, 2 done
-    unsigned char result[16] = {0};
+    unsigned char result[32] = {0};
+    int result_bytes = 16;                // 32 for integers on a PERM_FLAG_WIDE server
     int status = PERM_OK;
 };
 
@@ -72,14 +76,17 @@ struct Lane {
     unsigned char* h_in = nullptr;   // pinned staging of one batch's inputs
     unsigned char* d_in = nullptr;
     size_t in_cap = 0;
-    unsigned char* h_out = nullptr;  // pinned results (16 B) and statuses
+    unsigned char* h_out = nullptr;  // pinned results (up to 32 B each) and statuses
     unsigned char* d_out = nullptr;
     int* h_status = nullptr;
     int* d_status = nullptr;
     int out_cap = 0;
     std::vector<Request*> inflight;
+    std::vector<size_t> inflight_at;  // byte offset of each in-flight result in h_out
     std::atomic<bool> busy{false};
 };
+
+constexpr size_t kResultSlot = 32;   // bytes reserved per result in the lane buffers
 
 }  // namespace
 
@@ -93,6 +100,7 @@ struct perm_server_s {
     int queued = 0;
     std::atomic<bool> stop{false};
     std::atomic<bool> failed{false};
+    std::atomic<bool> abandon{false};   // process exit: the worker stops touching the device
     std::thread worker;
     Lane lanes[3];
     size_t table_budget = 0;
@@ -101,6 +109,28 @@ struct perm_server_s {
 
 namespace {
 
+// Servers whose perm_server_destroy timed out keep draining on their worker
+// thread.  At process exit those workers are told to stop and are joined before
+// the CUDA runtime tears itself down: the handler is registered with atexit
+// after the runtime was initialised, so it runs before the runtime's own exit
+// handlers.  The worker never waits on the device, so the join is prompt.
+std::mutex g_leaked_mu;
+std::vector<perm_server_t> g_leaked;
+std::once_flag g_leaked_once;
+
+void stop_leaked_workers() {
+    std::vector<perm_server_t> v;
+    {
+        std::lock_guard<std::mutex> g(g_leaked_mu);
+        v.swap(g_leaked);
+    }
+    for (perm_server_t s : v) {
+        s->abandon.store(true);
+        s->cv.notify_all();
+        if (s->worker.joinable()) s->worker.join();
+    }
+}
+
 bool lane_alloc(Lane& L, size_t in_cap, int out_cap) {
     if (cudaStreamCreateWithPriority(&L.stream, cudaStreamNonBlocking, L.priority) != cudaSuccess) return false;
     if (cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming) != cudaSuccess) return false;
@@ -108,8 +138,8 @@ bool lane_alloc(Lane& L, size_t in_cap, int out_cap) {
     L.out_cap = out_cap;
     if (cudaMallocHost(&L.h_in, in_cap) != cudaSuccess) return false;
     if (cudaMalloc(&L.d_in, in_cap) != cudaSuccess) return false;
-    if (cudaMallocHost(&L.h_out, (size_t)out_cap * 16) != cudaSuccess) return false;
-    if (cudaMalloc(&L.d_out, (size_t)out_cap * 16) != cudaSuccess) return false;
+    if (cudaMallocHost(&L.h_out, (size_t)out_cap * kResultSlot) != cudaSuccess) return false;
+    if (cudaMalloc(&L.d_out, (size_t)out_cap * kResultSlot) != cudaSuccess) return false;
     if (cudaMallocHost(&L.h_status, (size_t)out_cap * sizeof(int)) != cudaSuccess) return false;
     if (cudaMalloc(&L.d_status, (size_t)out_cap * sizeof(int)) != cudaSuccess) return false;
     return true;
@@ -130,6 +160,7 @@ void lane_free(Lane& L) {
     L.stream = nullptr; L.done = nullptr; L.ext_ws = nullptr; L.d_in = nullptr; L.d_out = nullptr;
     L.d_status = nullptr; L.h_in = nullptr; L.h_out = nullptr; L.h_status = nullptr;
     L.inflight.clear();
+    L.inflight_at.clear();
     L.busy = false;
 }
 
@@ -137,7 +168,7 @@ perm_plan_t lane_plan(perm_server_t s, Lane& L, int dtype, bool large) {
     const int k = dtype_slot(dtype);
     if (!L.plans[k]) {
         perm_opts o = s->opts;
-        o.flags = 0;
+        o.flags = dtype == PERM_C128 ? 0u : (s->opts.flags & PERM_FLAG_WIDE);
         o.method = L.method;
         o.max_batch = large ? 1 : kLaneBatch;
         if (!large) o.mem_budget_bytes = 0;   // the table budget applies to the large lane
@@ -155,19 +186,28 @@ perm_plan_t lane_plan(perm_server_t s, Lane& L, int dtype, bool large) {
 
 // Launch the requests `batch` (all of one lane) on the lane's stream.
 bool lane_launch(perm_server_t s, Lane& L, std::vector<Request*>& batch, bool large) {
-    // group by dtype: one perm_batch per dtype, inputs packed per group
-    size_t off = 0;
+    // group by dtype: one perm_batch per dtype, inputs packed per group; each group's
+    // results are packed at its own slot size (16 B, or 32 B for wide integers)
+    size_t off = 0, out_off = 0;
     int outpos = 0;
+    L.inflight.clear();
+    L.inflight_at.clear();
     for (int slot = 0; slot < 3; slot++) {
         const int dtype = slot == 0 ? PERM_C128 : (slot == 1 ? PERM_U01 : PERM_I64);
+        const size_t rbytes = (dtype != PERM_C128 && (s->opts.flags & PERM_FLAG_WIDE)) ? 32 : 16;
         std::vector<int> sizes;
         const size_t start = off;
-        const int out_start = outpos;
+        const size_t out_start = out_off;
+        const int status_start = outpos;
         for (Request* r : batch) {
             if (r->dtype != dtype) continue;
             std::memcpy(L.h_in + off, r->mat.data(), r->mat.size());
             off += r->mat.size();
             sizes.push_back(r->n);
+            r->result_bytes = (int)rbytes;
+            L.inflight.push_back(r);
+            L.inflight_at.push_back(out_off);
+            out_off += rbytes;
             outpos++;
         }
         if (sizes.empty()) continue;
@@ -176,24 +216,17 @@ bool lane_launch(perm_server_t s, Lane& L, std::vector<Request*>& batch, bool la
         if (cudaMemcpyAsync(L.d_in + start, L.h_in + start, off - start, cudaMemcpyHostToDevice,
                             L.stream) != cudaSuccess)
             return false;
-        if (perm_batch(p, L.d_in + start, sizes.data(), (int)sizes.size(), L.d_out + (size_t)out_start * 16,
-                       L.d_status + out_start, L.stream) != PERM_OK)
+        if (perm_batch(p, L.d_in + start, sizes.data(), (int)sizes.size(), L.d_out + out_start,
+                       L.d_status + status_start, L.stream) != PERM_OK)
             return false;
     }
     // results back in the same order (dtype groups)
-    if (cudaMemcpyAsync(L.h_out, L.d_out, (size_t)outpos * 16, cudaMemcpyDeviceToHost, L.stream) != cudaSuccess)
+    if (cudaMemcpyAsync(L.h_out, L.d_out, out_off, cudaMemcpyDeviceToHost, L.stream) != cudaSuccess)
         return false;
     if (cudaMemcpyAsync(L.h_status, L.d_status, (size_t)outpos * sizeof(int), cudaMemcpyDeviceToHost,
                         L.stream) != cudaSuccess)
         return false;
     if (cudaEventRecord(L.done, L.stream) != cudaSuccess) return false;
-    // remember the order the outputs were written in
-    L.inflight.clear();
-    for (int slot = 0; slot < 3; slot++) {
-        const int dtype = slot == 0 ? PERM_C128 : (slot == 1 ? PERM_U01 : PERM_I64);
-        for (Request* r : batch)
-            if (r->dtype == dtype) L.inflight.push_back(r);
-    }
     for (Request* r : batch) r->state.store(1, std::memory_order_relaxed);
     L.busy = true;
     return true;
@@ -202,11 +235,12 @@ bool lane_launch(perm_server_t s, Lane& L, std::vector<Request*>& batch, bool la
 void lane_complete(Lane& L) {
     for (size_t i = 0; i < L.inflight.size(); i++) {
         Request* r = L.inflight[i];
-        std::memcpy(r->result, L.h_out + i * 16, 16);
+        std::memcpy(r->result, L.h_out + L.inflight_at[i], (size_t)r->result_bytes);
         r->status = L.h_status[i];
         r->state.store(2, std::memory_order_release);
     }
     L.inflight.clear();
+    L.inflight_at.clear();
     L.busy = false;
 }
 
@@ -215,6 +249,7 @@ void worker_loop(perm_server_t s) {
     cudaGetDevice(&dev);
     std::vector<Request*> batch;
     while (true) {
+        if (s->abandon.load()) break;
         bool did = false;
         // completions
         for (int li = 0; li < 3; li++) {
@@ -341,8 +376,9 @@ perm_status perm_submit(perm_server_t s, const void* host_mat, int n, perm_dtype
         Request* raw = r.get();
         int lane = 0;
         if (n > kSmallN) {
-            // admission by table memory: Store-zechin if its chains fit the budget, else Ryser
-            const bool fits = n <= kMaxNSZ &&
+            // complex: admission by table memory, Store-zechin if its chains fit the budget,
+            // else Ryser; integers: Ryser (the method PERM_METHOD_AUTO picks for them)
+            const bool fits = auto_uses_sz(dtype) && n <= kMaxNSZ &&
                               sz_matrix_workspace_bytes(dtype, n, kLargeLow) + ((size_t)1 << 20) <= s->table_budget;
             lane = fits ? 1 : 2;
         }
@@ -354,14 +390,14 @@ perm_status perm_submit(perm_server_t s, const void* host_mat, int n, perm_dtype
     return PERM_OK;
 }
 
-perm_status perm_poll(perm_server_t s, uint64_t ticket, void* out16, int* item_status) {
-    if (!s || !out16) return PERM_EINVAL;
+perm_status perm_poll(perm_server_t s, uint64_t ticket, void* out, int* item_status) {
+    if (!s || !out) return PERM_EINVAL;
     std::lock_guard<std::mutex> g(s->mu);
     auto it = s->reqs.find(ticket);
     if (it == s->reqs.end()) return PERM_ENOTFOUND;
     Request* r = it->second.get();
     if (r->state.load(std::memory_order_acquire) != 2) return PERM_EAGAIN;
-    std::memcpy(out16, r->result, 16);
+    std::memcpy(out, r->result, (size_t)r->result_bytes);
     if (item_status) *item_status = r->status;
     const int st = r->status == PERM_ECUDA ? PERM_ECUDA : PERM_OK;
     s->reqs.erase(it);
@@ -389,7 +425,9 @@ perm_status perm_server_destroy(perm_server_t s, int timeout_ms) {
     if (result == PERM_ETIMEDOUT) {
         // leave the device work alone: the worker keeps draining in the background and
         // the server object is leaked rather than freed under running kernels
-        s->worker.detach();
+        std::call_once(g_leaked_once, [] { std::atexit(stop_leaked_workers); });
+        std::lock_guard<std::mutex> g(g_leaked_mu);
+        g_leaked.push_back(s);
         return PERM_ETIMEDOUT;
     }
     s->worker.join();

@@ -131,6 +131,7 @@ struct MatCtx {
     const int* hinfo;            // smem: [0..s) predecessor slots, [kBinomDim..) columns
     const unsigned short* masks; // mask list of this m (global)
     const unsigned* rowmask;     // smem: per row, the low columns with a nonzero entry
+    int out_words;               // integer result slot: 2 or 4 64-bit words
 };
 
 // Predecessor info for chain H: for the p-th outer element h_p (ascending),
@@ -397,8 +398,10 @@ __device__ void chain_int(const MatCtx& mc, int s, unsigned char* chain_smem,
                 if (gdst) gdst[idx] = val.lo;
             }
             if (last && l == m) {
-                out[2 * out_index] = val.lo;
-                out[2 * out_index + 1] = W128 ? val.hi : 0ull;
+                unsigned long long* dst = out + (size_t)mc.out_words * out_index;
+                dst[0] = val.lo;
+                dst[1] = W128 ? val.hi : 0ull;
+                if (mc.out_words == 4) { dst[2] = 0ull; dst[3] = 0ull; }
             }
         }
         off += cnt;
@@ -458,6 +461,7 @@ __device__ inline void init_ctx(MatCtx& mc, int n, int m_param, const unsigned c
     mc.hinfo = reinterpret_cast<const int*>(smem + L.hinfo_off);
     mc.masks = g_masks + ((1 << mc.m) - 2);
     mc.rowmask = reinterpret_cast<const unsigned*>(smem + L.rowmask_off);
+    mc.out_words = 2;
 }
 
 // Global-memory words of one chain.
@@ -542,7 +546,7 @@ sz_batched_c128(const double2* __restrict__ mats, const ItemDesc* __restrict__ i
 template <bool ZO, bool W64ONLY, int THREADS>
 __global__ void __launch_bounds__(THREADS, THREADS == 256 ? 3 : 2)
 sz_batched_int(const long long* __restrict__ mats, const ItemDesc* __restrict__ items, int count,
-               int m_param, unsigned long long* out, int* item_status,
+               int m_param, unsigned long long* out, int out_words, int* item_status,
                unsigned long long* workspace, size_t ws_words_per_cta, unsigned* counter) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_item;
@@ -560,6 +564,7 @@ sz_batched_int(const long long* __restrict__ mats, const ItemDesc* __restrict__ 
         const SmemLayout L = smem_layout(W64ONLY ? kU64 : kU128, n, sz_low_for(n, m_param));
         MatCtx mc;
         init_ctx(mc, n, m_param, smem, L);
+        mc.out_words = out_words;
         unsigned long long* coef = reinterpret_cast<unsigned long long*>(smem + L.coef_off);
         load_coef_int(mats + d.offset, n, mc.m, coef, reinterpret_cast<unsigned*>(smem + L.rowmask_off));
         __syncthreads();
@@ -606,7 +611,7 @@ sz_layer_c128(const double2* __restrict__ a, int n, int m_param, int s, double2*
 template <bool ZO>
 __global__ void __launch_bounds__(kThreadsInt, 3)
 sz_layer_int(const long long* __restrict__ a, int n, int m_param, int s, unsigned long long* out,
-             int out_index, int* item_status, unsigned long long* workspace) {
+             int out_words, int out_index, int* item_status, unsigned long long* workspace) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_width;
     fill_binom(reinterpret_cast<unsigned*>(smem));
@@ -614,6 +619,7 @@ sz_layer_int(const long long* __restrict__ a, int n, int m_param, int s, unsigne
     const SmemLayout L = smem_layout(kU128, n, sz_low_for(n, m_param));
     MatCtx mc;
     init_ctx(mc, n, m_param, smem, L);
+    mc.out_words = out_words;
     load_coef_int(a, n, mc.m, reinterpret_cast<unsigned long long*>(smem + L.coef_off),
                   reinterpret_cast<unsigned*>(smem + L.rowmask_off));
     __syncthreads();
@@ -639,7 +645,7 @@ sz_layer_int(const long long* __restrict__ a, int n, int m_param, int s, unsigne
         item_status[out_index] = width_status(w);
 }
 
-__global__ void trivial_kernel(int dtype, const ItemDesc* items, int count, void* out,
+__global__ void trivial_kernel(int dtype, const ItemDesc* items, int count, void* out, int out_words,
                                int* item_status) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= count) return;
@@ -647,15 +653,15 @@ __global__ void trivial_kernel(int dtype, const ItemDesc* items, int count, void
     if (dtype == PERM_C128) {
         reinterpret_cast<double2*>(out)[o] = make_double2(1.0, 0.0);
     } else {
-        reinterpret_cast<unsigned long long*>(out)[2 * o] = 1ull;
-        reinterpret_cast<unsigned long long*>(out)[2 * o + 1] = 0ull;
+        unsigned long long* dst = reinterpret_cast<unsigned long long*>(out) + (size_t)out_words * o;
+        for (int w = 0; w < out_words; w++) dst[w] = w == 0 ? 1ull : 0ull;
     }
     if (item_status) item_status[o] = PERM_OK;
 }
 
 // Kernel selection for the batched integer path.
-typedef void (*int_batched_fn)(const long long*, const ItemDesc*, int, int, unsigned long long*, int*,
-                               unsigned long long*, size_t, unsigned*);
+typedef void (*int_batched_fn)(const long long*, const ItemDesc*, int, int, unsigned long long*, int,
+                               int*, unsigned long long*, size_t, unsigned*);
 
 template <int T>
 int_batched_fn pick_int_batched_t(int dtype, int n_max) {
@@ -750,9 +756,9 @@ int sz_batched_occupancy(int dtype, int n_max, int m_param, int threads) {
 }
 
 cudaError_t sz_launch_batched(int dtype, const void* mats, const ItemDesc* items, int count,
-                              int n_max, int m, int threads, void* out, int* item_status,
-                              void* workspace, size_t ws_per_cta, int grid, unsigned* counter,
-                              cudaStream_t st) {
+                              int n_max, int m, int threads, void* out, int out_words,
+                              int* item_status, void* workspace, size_t ws_per_cta, int grid,
+                              unsigned* counter, cudaStream_t st) {
     if (count <= 0) return cudaSuccess;
     const int mm = sz_low_for(n_max, m);
     const int kind = batched_kind(dtype, n_max);
@@ -778,15 +784,15 @@ cudaError_t sz_launch_batched(int dtype, const void* mats, const ItemDesc* items
         e = set_smem((const void*)fn, smem);
         if (e != cudaSuccess) return e;
         fn<<<grid, ithreads, smem, st>>>((const long long*)mats, items, count, m,
-                                            (unsigned long long*)out, item_status,
+                                            (unsigned long long*)out, out_words, item_status,
                                             (unsigned long long*)workspace, ws_per_cta / 8, counter);
     }
     return cudaGetLastError();
 }
 
 cudaError_t sz_launch_single(int dtype, const void* mats, long long offset, int n, int m,
-                             int out_index, void* out, int* item_status, void* workspace,
-                             int grid_cap, cudaStream_t st) {
+                             int out_index, void* out, int out_words, int* item_status,
+                             void* workspace, int grid_cap, cudaStream_t st) {
     const int mm = sz_low_for(n, m);
     const int t = n - mm;
     const int smem = sz_smem_bytes(dtype, n, m);
@@ -802,12 +808,12 @@ cudaError_t sz_launch_single(int dtype, const void* mats, long long offset, int 
                 (unsigned long long*)workspace);
         } else if (dtype == PERM_U01) {
             sz_layer_int<true><<<grid, kThreadsInt, smem, st>>>(
-                (const long long*)mats + offset, n, m, s, (unsigned long long*)out, out_index,
-                item_status, (unsigned long long*)workspace);
+                (const long long*)mats + offset, n, m, s, (unsigned long long*)out, out_words,
+                out_index, item_status, (unsigned long long*)workspace);
         } else {
             sz_layer_int<false><<<grid, kThreadsInt, smem, st>>>(
-                (const long long*)mats + offset, n, m, s, (unsigned long long*)out, out_index,
-                item_status, (unsigned long long*)workspace);
+                (const long long*)mats + offset, n, m, s, (unsigned long long*)out, out_words,
+                out_index, item_status, (unsigned long long*)workspace);
         }
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -815,10 +821,10 @@ cudaError_t sz_launch_single(int dtype, const void* mats, long long offset, int 
     return cudaSuccess;
 }
 
-cudaError_t launch_trivial(int dtype, const ItemDesc* items, int count, void* out,
+cudaError_t launch_trivial(int dtype, const ItemDesc* items, int count, void* out, int out_words,
                            int* item_status, cudaStream_t st) {
     if (count <= 0) return cudaSuccess;
-    trivial_kernel<<<(count + 127) / 128, 128, 0, st>>>(dtype, items, count, out, item_status);
+    trivial_kernel<<<(count + 127) / 128, 128, 0, st>>>(dtype, items, count, out, out_words, item_status);
     return cudaGetLastError();
 }
 
@@ -906,7 +912,7 @@ extern "C" perm_status perm_sz_noalloc(const void* mat, int n, perm_dtype dtype,
         noalloc_write_one<<<1, 1, 0, st>>>(dtype, out, item_status);
         return cudaGetLastError() == cudaSuccess ? PERM_OK : PERM_ECUDA;
     }
-    const cudaError_t e = sz_launch_single(dtype, mat, 0, n, kNoAllocLow, 0, out, item_status,
+    const cudaError_t e = sz_launch_single(dtype, mat, 0, n, kNoAllocLow, 0, out, 2, item_status,
                                            scratch, sms, st);
     return e == cudaSuccess ? PERM_OK : PERM_ECUDA;
 }

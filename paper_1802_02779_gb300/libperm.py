@@ -26,6 +26,7 @@ METHOD_AUTO, METHOD_SZ, METHOD_RYSER = 0, 1, 2
 FLAG_PLAIN = 1
 FLAG_GRAPH = 2
 FLAG_AUTOTUNE = 4
+FLAG_WIDE = 8      # integer results as four uint64 words (256-bit slots), exact below 2^192
 
 DTYPES = {"c128": PERM_C128, "u01": PERM_U01, "i64": PERM_I64}
 
@@ -240,11 +241,20 @@ def u128_to_int(lo_hi) -> int:
     return lo | (hi << 64)
 
 
+def words_to_int(words) -> int:
+    """Unsigned integer from 64-bit words, least significant first (any count)."""
+    v = 0
+    for k, w in enumerate(words):
+        v |= (int(w) & 0xFFFFFFFFFFFFFFFF) << (64 * k)
+    return v
+
+
 def permanents(mats, dtype: Optional[str] = None, method: int = METHOD_AUTO, flags: int = 0,
                plan: Optional[Plan] = None, return_status: bool = False):
     """Permanents of a list of square numpy matrices (host in, host out).
 
-    Complex input -> numpy complex128 array; integer input -> list of Python ints.
+    Complex input -> numpy complex128 array; integer input -> list of Python ints
+    (with FLAG_WIDE in `flags`, or a wide `plan`, exact up to 2^192).
     """
     import torch
     mats = [np.asarray(m) for m in mats]
@@ -263,10 +273,11 @@ def permanents(mats, dtype: Optional[str] = None, method: int = METHOD_AUTO, fla
         plan = Plan(max(sizes) if sizes else 0, dtype, method=method, flags=flags)
     try:
         dev = torch.from_numpy(flat).cuda() if flat.size else torch.zeros(0, dtype=torch.complex128 if dtype == "c128" else torch.int64, device="cuda")
+        words = 4 if (flags & FLAG_WIDE or (not own and plan.describe().get("out_words") == 4)) else 2
         if dtype == "c128":
             out = torch.empty(len(mats), dtype=torch.complex128, device="cuda")
         else:
-            out = torch.empty((len(mats), 2), dtype=torch.int64, device="cuda")
+            out = torch.empty((len(mats), words), dtype=torch.int64, device="cuda")
         st = torch.empty(len(mats), dtype=torch.int32, device="cuda")
         plan.batch(dev, sizes, out, st)
         torch.cuda.synchronize()
@@ -275,16 +286,16 @@ def permanents(mats, dtype: Optional[str] = None, method: int = METHOD_AUTO, fla
     finally:
         if own:
             plan.close()
-    res = o if dtype == "c128" else [u128_to_int(r) for r in o]
+    res = o if dtype == "c128" else [words_to_int(r) for r in o]
     return (res, s) if return_status else res
 
 
 class Server:
     """The continuous-batching server (perm_server_*): submit host matrices, poll results."""
 
-    def __init__(self, mem_budget_bytes: int = 0, max_batch: int = 0):
+    def __init__(self, mem_budget_bytes: int = 0, max_batch: int = 0, flags: int = 0):
         lib = load()
-        opts = PermOpts(mem_budget_bytes, max_batch, METHOD_AUTO, 0, 0, 0)
+        opts = PermOpts(mem_budget_bytes, max_batch, METHOD_AUTO, flags, 0, 0)
         h = _VP()
         _check(lib.perm_server_create(ctypes.byref(opts), None, ctypes.byref(h)), "perm_server_create")
         self._h = h
@@ -310,7 +321,7 @@ class Server:
 
     def poll(self, ticket: int):
         """('done', (value, status)), ('pending', None) or ('missing', None)."""
-        buf = (ctypes.c_uint64 * 2)()
+        buf = (ctypes.c_uint64 * 4)()
         st = ctypes.c_int()
         rc = load().perm_poll(self._h, ctypes.c_uint64(ticket), buf, ctypes.byref(st))
         if rc == PERM_EAGAIN:
@@ -322,7 +333,7 @@ class Server:
         if dtype == "c128":
             v = np.frombuffer(bytes(buf), dtype=np.complex128)[0]
         else:
-            v = u128_to_int((buf[0], buf[1]))
+            v = words_to_int(tuple(buf))   # words the server did not write stay zero
         return "done", (v, st.value)
 
     def wait_all(self, tickets, timeout_s: float = 60.0, sleep_s: float = 0.0002):

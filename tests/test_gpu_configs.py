@@ -97,7 +97,7 @@ def test_serving_alone_vs_mix_large_orders(lp):
     small = [wl.gaussian_complex(12, 100 + k, scale=1 / 12) for k in range(20)]
     with lp.Server(mem_budget_bytes=8 << 30) as srv:
         t34 = srv.submit(a34, "c128")            # tables do not fit 8 GB: Ryser lane
-        t26 = srv.submit(b26, "u01")             # table lane
+        t26 = srv.submit(b26, "u01")             # integers: Ryser lane
         ts = [srv.submit(m, "c128") for m in small]
         res = srv.wait_all([t34, t26] + ts, timeout_s=600)
     assert all(st == lp.PERM_OK for _, st in res)
