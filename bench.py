@@ -31,7 +31,8 @@ sys.path.insert(0, ROOT)
 
 N = 20
 COUNT = 4096
-METRIC = "n=20 permanents/s (4096 complex128 + 4096 0/1 per step, batched Store-zechin)"
+METRIC = ("n=20 permanents/s (4096 complex128 by batched Store-zechin + 4096 0/1 exact "
+          "by the integer default, Ryser, per step)")
 UNIT = "permanents/s"
 WORKLOAD = ("n=20 batched: 4096 complex128 submatrices of a seeded 400x400 Haar unitary "
             "(rows 0..19, uniform sorted 20-column subsets) + 4096 seeded Bernoulli(0.5) 20x20 0/1 matrices")
@@ -53,6 +54,9 @@ def parse():
     ap.add_argument("--dtype", default="c128", choices=["c128", "u01"])
     ap.add_argument("--no-autotune", action="store_true",
                     help="use the default CTA size and chain width (profiling runs)")
+    ap.add_argument("--int-method", default="auto", choices=["auto", "sz"],
+                    help="method of the 0/1 half: auto (Ryser, the default for integers) or sz "
+                         "(the integer Store-zechin kernel; for profiling it)")
     return ap.parse_args()
 
 
@@ -113,10 +117,10 @@ class Clocks:
 
 
 # DRAM bytes (read + write) per n = 20 complex matrix of sz_batched_c128, from the ncu capture
-# summarised in profiles/sz_batched_c128_n20.md (304 matrices: 29.748599 GB + 7.624131 GB).
+# summarised in profiles/sz_batched_c128_n20.md (304 matrices: 29.751213 GB + 7.624846 GB).
 # Valid only for the kernel source it was measured on; otherwise the bench reports null.
-TRAFFIC_C128_PER_MATRIX = (29.755192e9 + 7.625324e9) / 304
-TRAFFIC_SOURCE_SHA256 = "237762c6d4437af68d2bf0cf8da3525c09c5aa2e8e11d82fdf97af5bfe4a08ae"
+TRAFFIC_C128_PER_MATRIX = (29.751213e9 + 7.624846e9) / 304
+TRAFFIC_SOURCE_SHA256 = "4678e78db4ed3234ecf1df8ab45a9f930fb56f513d4075e0842ddf5b789a6464"
 
 
 def traffic_per_launch(count: int):
@@ -244,7 +248,8 @@ def run_gpu(args, rank, world):
     i_st = torch.empty(count, dtype=torch.int32, device="cuda")
     tune = 0 if args.no_autotune else lp.FLAG_AUTOTUNE
     pc = lp.Plan(N, "c128", max_batch=count, flags=tune)
-    pi = lp.Plan(N, "u01", max_batch=count, flags=tune)
+    pi = lp.Plan(N, "u01", max_batch=count, flags=tune,
+                 method=lp.METHOD_SZ if args.int_method == "sz" else lp.METHOD_AUTO)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
@@ -339,8 +344,10 @@ def run_gpu(args, rank, world):
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": N, "complex128": count, "zero_one": count,
                        "method": {"complex128": "Store-zechin, persistent batched launch (one CTA per matrix)",
-                                  "zero_one": "Ryser Gray-code kernel (PERM_METHOD_AUTO's method for integers): "
-                                              "width kernel, one CTA per 2^17 codes, finishing kernel"},
+                                  "zero_one": ("Store-zechin batched integer kernel (--int-method sz)"
+                                               if args.int_method == "sz" else
+                                               "Ryser Gray-code kernel (PERM_METHOD_AUTO's method for integers): "
+                                               "width kernel, one CTA per 2^17 codes, finishing kernel")},
                        "l2": "flushed between timed steps (256 MB write)",
                        "plans": {"complex128": pc.describe(), "zero_one": pi.describe()},
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
@@ -348,8 +355,9 @@ def run_gpu(args, rank, world):
             "zero_one_perm_per_s": count / (float(np.mean(i_ms)) / 1000.0),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             # per step: the batched Store-zechin kernel (complex) and the Ryser width, Gray-code
-            # and finishing kernels (0/1, all 4096 matrices in one group)
-            "gpu_launches": 4 * args.steps, "clocks": ck}
+            # and finishing kernels (0/1, all matrices in one group), or one batched
+            # Store-zechin integer kernel with --int-method sz
+            "gpu_launches": (2 if args.int_method == "sz" else 4) * args.steps, "clocks": ck}
     line.update(extras)
     print(json.dumps(line), flush=True)
     if dist:

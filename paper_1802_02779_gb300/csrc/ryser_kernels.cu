@@ -45,7 +45,9 @@ __host__ __device__ inline long long parts_for(int dtype, int n) {
 }
 
 struct CPartial { double re_hi, re_lo, im_hi, im_lo; };
-// meta: item status in the low 32 bits, the width computed (0, 64, 128, 192) above
+// meta: item status in bits 0..31, the width computed (0, 64, 128, 192) in bits
+// 32..47, and the right shift the finished sum needs (n - 1 for Glynn's form,
+// else 0) in bits 48..55
 struct IPartial { unsigned long long w0, w1, w2, meta; };
 
 // ---------------------------------------------------------------------------
@@ -324,6 +326,98 @@ __device__ __forceinline__ void ryser_int_range(const E* __restrict__ s_col, uns
     acc[2] = a[2];
 }
 
+// ---------------------------------------------------------------------------
+// 0/1 matrices by Glynn's formula, exactly.  With d_0 = +1 and d_1..d_{n-1} in
+// {+1, -1},
+//     Sum_d (prod_k d_k) prod_i rho_i(d) = 2^{n-1} per(A),   rho_i(d) = sum_j d_j a_ij,
+// an identity over the integers (each permutation's term survives with
+// coefficient 2^{n-1}; every other monomial cancels).  The sum is therefore a
+// multiple of 2^{n-1}: computed modulo 2^{w+n-1} and shifted right by n-1 it
+// gives per(A) modulo 2^w exactly, over 2^{n-1} codes instead of Eq. (4)'s 2^n.
+// |rho_i| <= n, so a group of G rows with n^G < 2^31 multiplies exactly in
+// signed 32 bits; the group magnitudes multiply limb by limb modulo 2^{32 L},
+// L = ceil((w + n - 1) / 32), and the sign is applied when accumulating.
+// ---------------------------------------------------------------------------
+template <int N>
+constexpr int glynn_group() {
+    int g = 1;
+    unsigned long long p = N;
+    while (g < N && p * N < (1ull << 31)) {
+        p *= N;
+        g++;
+    }
+    return g;
+}
+
+// One thread's range of 2^log_len Glynn codes starting at g0: d_j = -1 iff bit
+// j - 1 of gray(code) is set.  s_col2[j * NP + i] = 2 a_ij, s_row[i] = sum_j a_ij.
+template <int N, int NP, int L>
+__device__ __forceinline__ void glynn_zo_range(const int* __restrict__ s_col2, const int* __restrict__ s_row,
+                                               unsigned long long g0, int log_len,
+                                               unsigned long long (&acc)[3]) {
+    constexpr int K = (L + 1) / 2;                 // 64-bit words of the accumulator
+    constexpr int G = glynn_group<N>();
+    constexpr int kGroups = (N + G - 1) / G;
+    unsigned long long gr = g0 ^ (g0 >> 1);
+    int r[N];
+#pragma unroll
+    for (int i = 0; i < N; i++) r[i] = s_row[i];
+    for (int j = 1; j < N; j++) {
+        if ((gr >> (j - 1)) & 1ull) {
+#pragma unroll
+            for (int i = 0; i < N; i++) r[i] -= s_col2[j * NP + i];
+        }
+    }
+    unsigned neg = (unsigned)__popcll(gr) & 1u;    // prod_k d_k = (-1)^neg
+    const unsigned long long len = 1ull << log_len;
+    unsigned long long a[3] = {acc[0], acc[1], acc[2]};
+    for (unsigned long long st = 0; st < len; st++) {
+        if (st > 0) {
+            const int b = __ffsll((long long)st) - 1;   // the same flip for the whole warp
+            gr ^= 1ull << b;
+            const int* col = s_col2 + (b + 1) * NP;
+            if ((gr >> b) & 1ull) {
+#pragma unroll
+                for (int i = 0; i < N; i++) r[i] -= col[i];
+            } else {
+#pragma unroll
+                for (int i = 0; i < N; i++) r[i] += col[i];
+            }
+            neg ^= 1u;
+        }
+        unsigned sgn = neg;
+        unsigned mag[kGroups];
+#pragma unroll
+        for (int q = 0; q < kGroups; q++) {
+            int g = r[q * G];
+#pragma unroll
+            for (int i = q * G + 1; i < q * G + G && i < N; i++) g *= r[i];
+            sgn ^= (unsigned)g >> 31;
+            mag[q] = (unsigned)abs(g);
+        }
+        unsigned p[L];
+        p[0] = mag[0];
+#pragma unroll
+        for (int k = 1; k < L; k++) p[k] = 0u;
+#pragma unroll
+        for (int q = 1; q < kGroups; q++) limbs_mul_u32<L>(p, mag[q]);
+        // x = (sgn ? -|P| : |P|) modulo 2^(64 K): complement and add the sign bit
+        const unsigned long long m = 0ull - (unsigned long long)sgn;
+        unsigned long long x[3] = {0ull, 0ull, 0ull};
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            const unsigned long long hi = (2 * k + 1 < L) ? ((unsigned long long)p[2 * k + 1] << 32) : 0ull;
+            x[k] = ((unsigned long long)p[2 * k] | hi) ^ m;
+        }
+        words_add<K>(a, x);
+        const unsigned long long c[3] = {(unsigned long long)sgn, 0ull, 0ull};
+        words_add<K>(a, c);
+    }
+    acc[0] = a[0];
+    acc[1] = a[1];
+    acc[2] = a[2];
+}
+
 // Widest modulus an order-N matrix of the given kind can need: a 0/1 matrix
 // has per(A) <= n!, and 20! < 2^64, 34! < 2^128, 40! < 2^192.
 template <int N, bool ZO>
@@ -338,7 +432,10 @@ ryser_int_kernel(const long long* __restrict__ mats, const ItemDesc* __restrict_
                  IPartial* __restrict__ partials) {
     using E = typename std::conditional<ZO, unsigned, unsigned long long>::type;
     constexpr int NP = ZO ? ((N + 3) & ~3) : ((N + 1) & ~1);   // 16-byte columns
-    __shared__ __align__(16) E s_col[N * NP];                   // s_col[j * NP + i] = a_ij
+    constexpr bool kEq4 = !ZO || N >= 35;                       // Eq. (4) codes needed (192 bits)
+    __shared__ __align__(16) E s_col[kEq4 ? N * NP : 1];        // s_col[j * NP + i] = a_ij
+    __shared__ __align__(16) int s_col2[ZO ? N * NP : 1];       // 0/1, Glynn: 2 a_ij
+    __shared__ int s_row[ZO ? NP : 1];                          // 0/1, Glynn: sum_j a_ij
     __shared__ unsigned long long s_acc[3][kRyserThreads];
     __shared__ int s_width;
     constexpr int G = N;
@@ -346,6 +443,11 @@ ryser_int_kernel(const long long* __restrict__ mats, const ItemDesc* __restrict_
     constexpr int kLogPart = (G > kLogCodesPerPart) ? kLogCodesPerPart : G;
     constexpr int kLogThr = kLogPart >= 8 ? 8 : kLogPart;
     constexpr int kLogLen = kLogPart - kLogThr;
+    // Glynn (0/1, widths 64 and 128): a piece holds half as many codes
+    constexpr int kLogPartG = kLogPart - 1;
+    constexpr int kLogThrG = kLogPartG >= 8 ? 8 : kLogPartG;
+    constexpr int kLogLenG = kLogPartG - kLogThrG;
+    constexpr int kL64 = (64 + N - 1 + 31) / 32, kL128 = (128 + N - 1 + 31) / 32;
     constexpr int kMaxW = max_width<N, ZO>();
 
     for (long long task = blockIdx.x; task < total_parts; task += gridDim.x) {
@@ -355,7 +457,15 @@ ryser_int_kernel(const long long* __restrict__ mats, const ItemDesc* __restrict_
         __syncthreads();
         for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
             const int i = e / N, j = e % N;
-            s_col[j * NP + i] = (E)a[e];
+            if constexpr (kEq4) s_col[j * NP + i] = (E)a[e];
+            if constexpr (ZO) s_col2[j * NP + i] = 2 * (int)a[e];
+        }
+        if constexpr (ZO) {
+            if (threadIdx.x < N) {
+                int rs = 0;
+                for (int j = 0; j < N; j++) rs += (int)a[threadIdx.x * N + j];
+                s_row[threadIdx.x] = rs;
+            }
         }
         if (threadIdx.x == 0) s_width = widths[task / kParts];
         __syncthreads();
@@ -363,16 +473,32 @@ ryser_int_kernel(const long long* __restrict__ mats, const ItemDesc* __restrict_
         // width computed: the decided one; past the bound, the widest the output holds
         int cw = w == kWidthInvalid ? 0 : (w == kWidthOverflow ? (allow192 ? 192 : 128) : w);
         if (cw > kMaxW) cw = kMaxW;
+        int shift = 0;                  // Glynn: the sum is 2^(n-1) per(A)
         unsigned long long acc[3] = {0ull, 0ull, 0ull};
-        if (threadIdx.x < (1 << kLogThr) && cw > 0) {
-            const unsigned long long g0 =
-                ((unsigned long long)part << kLogPart) + ((unsigned long long)threadIdx.x << kLogLen);
-            if (cw == 64) ryser_int_range<N, NP, 64>(s_col, g0, kLogLen, acc);
-            if constexpr (kMaxW >= 128) {
-                if (cw == 128) ryser_int_range<N, NP, 128>(s_col, g0, kLogLen, acc);
+        if constexpr (ZO) {
+            if (cw == 64 || cw == 128) {
+                shift = N - 1;
+                if (threadIdx.x < (1 << kLogThrG)) {
+                    const unsigned long long g0 = ((unsigned long long)part << kLogPartG) +
+                                                  ((unsigned long long)threadIdx.x << kLogLenG);
+                    if (cw == 64) glynn_zo_range<N, NP, kL64>(s_col2, s_row, g0, kLogLenG, acc);
+                    if constexpr (kMaxW >= 128) {
+                        if (cw == 128) glynn_zo_range<N, NP, kL128>(s_col2, s_row, g0, kLogLenG, acc);
+                    }
+                }
             }
-            if constexpr (kMaxW >= 192) {
-                if (cw == 192) ryser_int_range<N, NP, 192>(s_col, g0, kLogLen, acc);
+        }
+        if constexpr (kEq4) {
+            if (shift == 0 && threadIdx.x < (1 << kLogThr) && cw > 0) {
+                const unsigned long long g0 =
+                    ((unsigned long long)part << kLogPart) + ((unsigned long long)threadIdx.x << kLogLen);
+                if constexpr (!ZO) {
+                    if (cw == 64) ryser_int_range<N, NP, 64>(s_col, g0, kLogLen, acc);
+                    if (cw == 128) ryser_int_range<N, NP, 128>(s_col, g0, kLogLen, acc);
+                }
+                if constexpr (kMaxW >= 192) {
+                    if (cw == 192) ryser_int_range<N, NP, 192>(s_col, g0, kLogLen, acc);
+                }
             }
         }
         s_acc[0][threadIdx.x] = acc[0];
@@ -396,7 +522,8 @@ ryser_int_kernel(const long long* __restrict__ mats, const ItemDesc* __restrict_
             p.w0 = s_acc[0][0];
             p.w1 = s_acc[1][0];
             p.w2 = s_acc[2][0];
-            p.meta = (unsigned long long)(unsigned)width_status(w) | ((unsigned long long)cw << 32);
+            p.meta = (unsigned long long)(unsigned)width_status(w) | ((unsigned long long)cw << 32) |
+                     ((unsigned long long)shift << 48);
             partials[task] = p;
         }
     }
@@ -467,13 +594,20 @@ __global__ void ryser_finish_int(const ItemDesc* items, long long parts, int cou
     if (threadIdx.x == 0) {
         const unsigned long long meta = partials[b].meta;   // the same for every piece of the matrix
         const int st = (int)(unsigned)(meta & 0xffffffffull);
-        const int cw = (int)(meta >> 32);
+        const int cw = (int)((meta >> 32) & 0xffffull);
+        const int sh = (int)((meta >> 48) & 0xffull);
+        unsigned long long v0 = s[0][0], v1 = s[1][0], v2 = s[2][0];
+        if (sh > 0) {       // exact division of Glynn's sum by 2^(n-1)
+            v0 = (v0 >> sh) | (v1 << (64 - sh));
+            v1 = (v1 >> sh) | (v2 << (64 - sh));
+            v2 >>= sh;
+        }
         const int o = items[it].out_index;
         unsigned long long* dst = out + (size_t)out_words * o;
-        dst[0] = cw >= 64 ? s[0][0] : 0ull;
-        dst[1] = cw >= 128 ? s[1][0] : 0ull;
+        dst[0] = cw >= 64 ? v0 : 0ull;
+        dst[1] = cw >= 128 ? v1 : 0ull;
         if (out_words == 4) {
-            dst[2] = cw >= 192 ? s[2][0] : 0ull;
+            dst[2] = cw >= 192 ? v2 : 0ull;
             dst[3] = 0ull;
         }
         if (item_status) item_status[o] = st;

@@ -163,3 +163,29 @@ def test_server_wide(lp):
     assert res[1] == (120, lp.PERM_OK)
     assert res[2][0] == lp.permanents([c5], "c128")[0] and res[2][1] == lp.PERM_OK
     assert res[3] == (2 ** 30 * math.factorial(30), lp.PERM_OK)
+
+
+# ---------------------------------------------------------------------------
+# 0/1 Ryser by Glynn's formula modulo 2^(w + n - 1), shifted by n - 1
+# ---------------------------------------------------------------------------
+def test_glynn_ones_every_order(lp):
+    ns = list(range(1, 35))
+    res, st = lp.permanents([np.ones((n, n), np.int64) for n in ns], "u01", return_status=True)
+    assert list(st) == [lp.PERM_OK] * len(ns)
+    assert res == [math.factorial(n) for n in ns]
+
+
+def test_glynn_against_store_zechin(lp):
+    mats = [rand01(n, 500 + n, p=0.3 + 0.4 * (n % 3) / 2) for n in range(1, 25)]
+    auto = lp.permanents(mats, "u01")
+    sz = lp.permanents(mats, "u01", method=lp.METHOD_SZ)
+    assert auto == sz
+
+
+@pytest.mark.parametrize("n,size,seed", [(28, 9, 11), (31, 16, 12), (34, 10, 13)])
+def test_glynn_128_against_rook_numbers(lp, n, size, seed):
+    cells = random_board(n, size, seed)
+    want = per_complement(n, cells)
+    assert 2 ** 64 < want < 2 ** 128
+    res, st = lp.permanents([complement_matrix(n, cells)], "u01", return_status=True)
+    assert st[0] == lp.PERM_OK and res[0] == want
