@@ -288,26 +288,28 @@ template <int N, int NP, int W, typename E>
 __device__ __forceinline__ void ryser_int_range(const E* __restrict__ s_col, unsigned long long g0,
                                                 int log_len, unsigned long long (&acc)[3]) {
     constexpr int K = W / 64;
-    unsigned long long gr = g0 ^ (g0 >> 1);
+    const unsigned long long gr0 = g0 ^ (g0 >> 1);
     E r[N];
 #pragma unroll
     for (int i = 0; i < N; i++) r[i] = 0;
     for (int j = 0; j < N; j++) {
-        if ((gr >> j) & 1ull) {
+        if ((gr0 >> j) & 1ull) {
 #pragma unroll
             for (int i = 0; i < N; i++) r[i] += s_col[j * NP + i];
         }
     }
     // sign (-1)^(n - |S|)
-    int neg = (N - __popcll(gr)) & 1;
-    const unsigned long long len = 1ull << log_len;
+    int neg = (N - __popcll(gr0)) & 1;
+    // log_len <= 9 and g0 is a multiple of 2^log_len: the walk flips only low bits
+    unsigned grl = (unsigned)gr0;
+    const unsigned len = 1u << log_len;
     unsigned long long a[3] = {acc[0], acc[1], acc[2]};
-    for (unsigned long long st = 0; st < len; st++) {
+    for (unsigned st = 0; st < len; st++) {
         if (st > 0) {
-            const int j = __ffsll((long long)st) - 1;   // the same column for the whole warp
-            gr ^= 1ull << j;
+            const int j = __ffs(st) - 1;                // the same column for the whole warp
+            grl ^= 1u << j;
             const E* col = s_col + j * NP;
-            if ((gr >> j) & 1ull) {
+            if ((grl >> j) & 1u) {
 #pragma unroll
                 for (int i = 0; i < N; i++) r[i] += col[i];
             } else {
@@ -351,6 +353,15 @@ constexpr int glynn_group() {
 
 // One thread's range of 2^log_len Glynn codes starting at g0: d_j = -1 iff bit
 // j - 1 of gray(code) is set.  s_col2[j * NP + i] = 2 a_ij, s_row[i] = sum_j a_ij.
+// log_len <= 8, and g0 is a multiple of 2^log_len, so the walk flips only the
+// low 8 bits of the Gray code (32-bit counters).
+//
+// Most terms vanish: rho_i is a sum of +-1 over the ones of row i, zero for
+// about a quarter of the sign vectors at density 1/2, so at n = 20 over 99% of
+// the products are zero.  A zero group product skips the wide product and the
+// accumulation (a branch that is uniform for most warps).  A negative term is
+// added as the complement of its magnitude, and the +1 each complement lacks
+// is added once at the end from a count.
 template <int N, int NP, int L>
 __device__ __forceinline__ void glynn_zo_range(const int* __restrict__ s_col2, const int* __restrict__ s_row,
                                                unsigned long long g0, int log_len,
@@ -358,25 +369,27 @@ __device__ __forceinline__ void glynn_zo_range(const int* __restrict__ s_col2, c
     constexpr int K = (L + 1) / 2;                 // 64-bit words of the accumulator
     constexpr int G = glynn_group<N>();
     constexpr int kGroups = (N + G - 1) / G;
-    unsigned long long gr = g0 ^ (g0 >> 1);
+    const unsigned long long gr0 = g0 ^ (g0 >> 1);
     int r[N];
 #pragma unroll
     for (int i = 0; i < N; i++) r[i] = s_row[i];
     for (int j = 1; j < N; j++) {
-        if ((gr >> (j - 1)) & 1ull) {
+        if ((gr0 >> (j - 1)) & 1ull) {
 #pragma unroll
             for (int i = 0; i < N; i++) r[i] -= s_col2[j * NP + i];
         }
     }
-    unsigned neg = (unsigned)__popcll(gr) & 1u;    // prod_k d_k = (-1)^neg
-    const unsigned long long len = 1ull << log_len;
+    unsigned neg = (unsigned)__popcll(gr0) & 1u;   // prod_k d_k = (-1)^neg
+    unsigned grl = (unsigned)gr0;                   // low word of the Gray code
+    unsigned ncount = 0;                            // negative terms added as complements
+    const unsigned len = 1u << log_len;
     unsigned long long a[3] = {acc[0], acc[1], acc[2]};
-    for (unsigned long long st = 0; st < len; st++) {
+    for (unsigned st = 0; st < len; st++) {
         if (st > 0) {
-            const int b = __ffsll((long long)st) - 1;   // the same flip for the whole warp
-            gr ^= 1ull << b;
+            const int b = __ffs(st) - 1;            // the same flip for the whole warp
+            grl ^= 1u << b;
             const int* col = s_col2 + (b + 1) * NP;
-            if ((gr >> b) & 1ull) {
+            if ((grl >> b) & 1u) {
 #pragma unroll
                 for (int i = 0; i < N; i++) r[i] -= col[i];
             } else {
@@ -385,34 +398,167 @@ __device__ __forceinline__ void glynn_zo_range(const int* __restrict__ s_col2, c
             }
             neg ^= 1u;
         }
-        unsigned sgn = neg;
-        unsigned mag[kGroups];
+        int g[kGroups];
+        bool nonzero = true;
 #pragma unroll
         for (int q = 0; q < kGroups; q++) {
-            int g = r[q * G];
+            g[q] = r[q * G];
 #pragma unroll
-            for (int i = q * G + 1; i < q * G + G && i < N; i++) g *= r[i];
-            sgn ^= (unsigned)g >> 31;
-            mag[q] = (unsigned)abs(g);
+            for (int i = q * G + 1; i < q * G + G && i < N; i++) g[q] *= r[i];
+            nonzero = nonzero && g[q] != 0;
         }
-        unsigned p[L];
-        p[0] = mag[0];
+        if (nonzero) {
+            unsigned sgn = neg;
+            unsigned p[L];
 #pragma unroll
-        for (int k = 1; k < L; k++) p[k] = 0u;
+            for (int q = 0; q < kGroups; q++) sgn ^= (unsigned)g[q] >> 31;
+            p[0] = (unsigned)abs(g[0]);
 #pragma unroll
-        for (int q = 1; q < kGroups; q++) limbs_mul_u32<L>(p, mag[q]);
-        // x = (sgn ? -|P| : |P|) modulo 2^(64 K): complement and add the sign bit
-        const unsigned long long m = 0ull - (unsigned long long)sgn;
-        unsigned long long x[3] = {0ull, 0ull, 0ull};
+            for (int k = 1; k < L; k++) p[k] = 0u;
 #pragma unroll
-        for (int k = 0; k < K; k++) {
-            const unsigned long long hi = (2 * k + 1 < L) ? ((unsigned long long)p[2 * k + 1] << 32) : 0ull;
-            x[k] = ((unsigned long long)p[2 * k] | hi) ^ m;
+            for (int q = 1; q < kGroups; q++) limbs_mul_u32<L>(p, (unsigned)abs(g[q]));
+            // sgn ? ~|P| : |P| modulo 2^(64 K); the missing +1 of -|P| = ~|P| + 1 is counted
+            const unsigned long long m = 0ull - (unsigned long long)sgn;
+            unsigned long long x[3] = {0ull, 0ull, 0ull};
+#pragma unroll
+            for (int k = 0; k < K; k++) {
+                const unsigned long long hi = (2 * k + 1 < L) ? ((unsigned long long)p[2 * k + 1] << 32) : 0ull;
+                x[k] = ((unsigned long long)p[2 * k] | hi) ^ m;
+            }
+            words_add<K>(a, x);
+            ncount += sgn;
         }
-        words_add<K>(a, x);
-        const unsigned long long c[3] = {(unsigned long long)sgn, 0ull, 0ull};
-        words_add<K>(a, c);
     }
+    const unsigned long long c[3] = {(unsigned long long)ncount, 0ull, 0ull};
+    words_add<K>(a, c);
+    acc[0] = a[0];
+    acc[1] = a[1];
+    acc[2] = a[2];
+}
+
+// Bit-sliced variant for 12 <= n <= 32 (full warps, one 32-bit word per row set).
+// Let c_i be the number of ones of row i among the columns with d_j = -1, so that
+// rho_i = R_i - 2 c_i.  A thread keeps the c_i of all rows as bit planes
+// (plane k holds bit k of every c_i): flipping column j adds or subtracts the
+// column's row mask with a ripple over the planes, and "some rho_i = 0" is the
+// plane-wise test c_i == R_i / 2 over the rows of even R_i -- a few logical
+// operations per code for every row at once.  The codes whose product is
+// nonzero (about 6% at density 1/2, n = 20) go into a per-warp queue; every 32
+// queued codes are evaluated by the whole warp from scratch (rho_i by popcount of
+// the code against row i's ones), so the rare wide products keep all lanes busy.
+template <int N>
+constexpr int count_planes() {
+    int p = 1;
+    while ((1 << p) <= N) p++;
+    return p;                     // bits of 0..N
+}
+
+// The Glynn term of one code (d_j = -1 iff bit j - 1 of `code`), added to `a` as
+// described for glynn_zo_range.  s_rm[i]: bit j - 1 set iff a_ij = 1 (j >= 1).
+template <int N, int L>
+__device__ __forceinline__ void glynn_term_from_code(unsigned code, const unsigned* __restrict__ s_rm,
+                                                     const int* __restrict__ s_row,
+                                                     unsigned long long (&a)[3], unsigned& ncount) {
+    constexpr int K = (L + 1) / 2;
+    constexpr int G = glynn_group<N>();
+    constexpr int kGroups = (N + G - 1) / G;
+    unsigned sgn = (unsigned)__popc(code) & 1u;
+    int g[kGroups];
+#pragma unroll
+    for (int q = 0; q < kGroups; q++) {
+        g[q] = s_row[q * G] - 2 * __popc(code & s_rm[q * G]);
+#pragma unroll
+        for (int i = q * G + 1; i < q * G + G && i < N; i++) g[q] *= s_row[i] - 2 * __popc(code & s_rm[i]);
+        sgn ^= (unsigned)g[q] >> 31;
+    }
+    unsigned p[L];
+    p[0] = (unsigned)abs(g[0]);
+#pragma unroll
+    for (int k = 1; k < L; k++) p[k] = 0u;
+#pragma unroll
+    for (int q = 1; q < kGroups; q++) limbs_mul_u32<L>(p, (unsigned)abs(g[q]));
+    const unsigned long long m = 0ull - (unsigned long long)sgn;
+    unsigned long long x[3] = {0ull, 0ull, 0ull};
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        const unsigned long long hi = (2 * k + 1 < L) ? ((unsigned long long)p[2 * k + 1] << 32) : 0ull;
+        x[k] = ((unsigned long long)p[2 * k] | hi) ^ m;
+    }
+    words_add<K>(a, x);
+    ncount += sgn;
+}
+
+// One thread's range of 2^log_len codes from g0 (a multiple of 2^log_len);
+// called by every lane of full warps with the same log_len.  q: this warp's
+// 64-entry queue.  s_cm[j]: bit i set iff a_ij = 1.
+template <int N, int L>
+__device__ __forceinline__ void glynn_bits_range(const unsigned* __restrict__ s_cm, const unsigned* __restrict__ s_rm,
+                                                 const int* __restrict__ s_row, unsigned* q,
+                                                 unsigned g0, int log_len, unsigned long long (&acc)[3]) {
+    constexpr int K = (L + 1) / 2;
+    constexpr int NPL = count_planes<N>();
+    const unsigned lane = threadIdx.x & 31u;
+    unsigned gr = g0 ^ (g0 >> 1);
+    // target planes: rows of even R_i, h_i = R_i / 2
+    unsigned H[NPL], P[NPL];
+    unsigned even = 0u;
+#pragma unroll
+    for (int k = 0; k < NPL; k++) { H[k] = 0u; P[k] = 0u; }
+#pragma unroll
+    for (int i = 0; i < N; i++) {
+        const int R = s_row[i];
+        const unsigned c = (unsigned)__popc(gr & s_rm[i]);
+        if ((R & 1) == 0) even |= 1u << i;
+#pragma unroll
+        for (int k = 0; k < NPL; k++) {
+            H[k] |= (((unsigned)(R >> 1) >> k) & 1u) << i;
+            P[k] |= ((c >> k) & 1u) << i;
+        }
+    }
+    unsigned qn = 0;                 // entries in the queue (the same in every lane)
+    unsigned ncount = 0;
+    unsigned long long a[3] = {acc[0], acc[1], acc[2]};
+    const unsigned len = 1u << log_len;
+    for (unsigned st = 0; st < len; st++) {
+        if (st > 0) {
+            const int b = __ffs(st) - 1;     // the same flip for the whole warp
+            gr ^= 1u << b;
+            const unsigned M = s_cm[b + 1];
+            if ((gr >> b) & 1u) {            // d_{b+1}: +1 -> -1, c_i += 1 on the rows of M
+                unsigned cy = M;
+#pragma unroll
+                for (int k = 0; k < NPL; k++) { const unsigned t = P[k] & cy; P[k] ^= cy; cy = t; }
+            } else {                         // -1 -> +1, c_i -= 1
+                unsigned bw = M;
+#pragma unroll
+                for (int k = 0; k < NPL; k++) { const unsigned t = ~P[k] & bw; P[k] ^= bw; bw = t; }
+            }
+        }
+        unsigned diff = 0u;
+#pragma unroll
+        for (int k = 0; k < NPL; k++) diff |= P[k] ^ H[k];
+        const bool live = (even & ~diff) == 0u;   // no rho_i is zero
+        const unsigned ball = __ballot_sync(0xffffffffu, live);
+        if (ball) {
+            if (live) q[qn + __popc(ball & ((1u << lane) - 1u))] = gr;
+            qn += (unsigned)__popc(ball);
+            if (qn >= 32u) {
+                __syncwarp();
+                const unsigned code = q[lane];
+                const unsigned rest = lane < qn - 32u ? q[32u + lane] : 0u;
+                __syncwarp();
+                if (lane < qn - 32u) q[lane] = rest;
+                qn -= 32u;
+                __syncwarp();
+                glynn_term_from_code<N, L>(code, s_rm, s_row, a, ncount);
+            }
+        }
+    }
+    __syncwarp();
+    if (lane < qn) glynn_term_from_code<N, L>(q[lane], s_rm, s_row, a, ncount);
+    __syncwarp();
+    const unsigned long long c[3] = {(unsigned long long)ncount, 0ull, 0ull};
+    words_add<K>(a, c);
     acc[0] = a[0];
     acc[1] = a[1];
     acc[2] = a[2];
@@ -426,7 +572,7 @@ constexpr int max_width() {
 }
 
 template <int N, bool ZO>
-__global__ void __launch_bounds__(kRyserThreads)
+__global__ void __launch_bounds__(kRyserThreads, ZO ? 3 : 1)
 ryser_int_kernel(const long long* __restrict__ mats, const ItemDesc* __restrict__ items,
                  long long total_parts, const int* __restrict__ widths, int allow192,
                  IPartial* __restrict__ partials) {
@@ -436,6 +582,10 @@ ryser_int_kernel(const long long* __restrict__ mats, const ItemDesc* __restrict_
     __shared__ __align__(16) E s_col[kEq4 ? N * NP : 1];        // s_col[j * NP + i] = a_ij
     __shared__ __align__(16) int s_col2[ZO ? N * NP : 1];       // 0/1, Glynn: 2 a_ij
     __shared__ int s_row[ZO ? NP : 1];                          // 0/1, Glynn: sum_j a_ij
+    constexpr bool kBits = ZO && N >= 12 && N <= 32;            // bit-sliced Glynn walk
+    __shared__ unsigned s_cm[kBits ? N : 1];                    // bit i: a_ij = 1
+    __shared__ unsigned s_rm[kBits ? N : 1];                    // bit j - 1: a_ij = 1 (j >= 1)
+    __shared__ unsigned s_q[kBits ? kRyserThreads / 32 : 1][kBits ? 64 : 1];   // per-warp queues
     __shared__ unsigned long long s_acc[3][kRyserThreads];
     __shared__ int s_width;
     constexpr int G = N;
@@ -467,6 +617,16 @@ ryser_int_kernel(const long long* __restrict__ mats, const ItemDesc* __restrict_
                 s_row[threadIdx.x] = rs;
             }
         }
+        if constexpr (kBits) {
+            if (threadIdx.x < N) {
+                const int t = threadIdx.x;
+                unsigned cm = 0u, rm = 0u;
+                for (int i = 0; i < N; i++) cm |= (a[i * N + t] != 0 ? 1u : 0u) << i;
+                for (int j = 1; j < N; j++) rm |= (a[t * N + j] != 0 ? 1u : 0u) << (j - 1);
+                s_cm[t] = cm;
+                s_rm[t] = rm;
+            }
+        }
         if (threadIdx.x == 0) s_width = widths[task / kParts];
         __syncthreads();
         const int w = s_width;
@@ -481,9 +641,19 @@ ryser_int_kernel(const long long* __restrict__ mats, const ItemDesc* __restrict_
                 if (threadIdx.x < (1 << kLogThrG)) {
                     const unsigned long long g0 = ((unsigned long long)part << kLogPartG) +
                                                   ((unsigned long long)threadIdx.x << kLogLenG);
-                    if (cw == 64) glynn_zo_range<N, NP, kL64>(s_col2, s_row, g0, kLogLenG, acc);
-                    if constexpr (kMaxW >= 128) {
-                        if (cw == 128) glynn_zo_range<N, NP, kL128>(s_col2, s_row, g0, kLogLenG, acc);
+                    if constexpr (kBits) {
+                        // every thread of the CTA takes part (kLogThrG = 8): full warps
+                        unsigned* q = s_q[threadIdx.x >> 5];
+                        if (cw == 64) glynn_bits_range<N, kL64>(s_cm, s_rm, s_row, q, (unsigned)g0, kLogLenG, acc);
+                        if constexpr (kMaxW >= 128) {
+                            if (cw == 128)
+                                glynn_bits_range<N, kL128>(s_cm, s_rm, s_row, q, (unsigned)g0, kLogLenG, acc);
+                        }
+                    } else {
+                        if (cw == 64) glynn_zo_range<N, NP, kL64>(s_col2, s_row, g0, kLogLenG, acc);
+                        if constexpr (kMaxW >= 128) {
+                            if (cw == 128) glynn_zo_range<N, NP, kL128>(s_col2, s_row, g0, kLogLenG, acc);
+                        }
                     }
                 }
             }
