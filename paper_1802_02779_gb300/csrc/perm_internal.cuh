@@ -133,6 +133,66 @@ __device__ inline int decide_width(const long long* a, int n, bool zero_one, boo
     return kWidthOverflow;
 }
 
+// decide_width for one matrix by a whole warp (every lane calls it, with the
+// same arguments).  Lanes compute the row and column terms; lane 0 combines
+// them in the order decide_width uses, so every decision (and every rounding of
+// the log2 sums) is identical to it.  The result is returned to every lane.
+__device__ inline int decide_width_warp(const long long* a, int n, bool zero_one, bool allow192) {
+    const int lane = threadIdx.x & 31;
+    unsigned long long rs_mine[2] = {0ull, 0ull}, cs_mine[2] = {0ull, 0ull};
+    double lr_mine[2] = {0.0, 0.0}, bt_mine[2] = {0.0, 0.0}, lc_mine[2] = {0.0, 0.0};
+    bool bad = false;
+    for (int h = 0; h < 2; h++) {
+        const int i = lane + 32 * h;
+        if (i < n) {
+            unsigned long long rs = 0, cs = 0;
+            for (int j = 0; j < n; j++) {
+                const long long v = a[(size_t)i * n + j];
+                if (v < 0 || (zero_one && v > 1) || v > (1ll << 40)) bad = true;
+                rs += (unsigned long long)v;
+                cs += (unsigned long long)a[(size_t)j * n + i];
+            }
+            rs_mine[h] = rs;
+            cs_mine[h] = cs;
+            lr_mine[h] = log2((double)rs);
+            lc_mine[h] = log2((double)cs);
+            if (zero_one && rs > 1) {
+                double lf = 0.0;
+                for (unsigned long long q = 2; q <= rs; q++) lf += log2((double)q);
+                bt_mine[h] = lf / (double)rs;
+            }
+        }
+    }
+    if (__any_sync(0xffffffffu, bad)) return kWidthInvalid;
+    unsigned __int128 prow = 1, pcol = 1;
+    double breg = 0.0, lrow = 0.0, lcol = 0.0;
+    for (int i = 0; i < n; i++) {               // row (and column) order, as decide_width
+        const int src = i & 31, h = i >> 5;
+        const unsigned long long rs = __shfl_sync(0xffffffffu, rs_mine[h], src);
+        const unsigned long long cs = __shfl_sync(0xffffffffu, cs_mine[h], src);
+        const double lr = __shfl_sync(0xffffffffu, lr_mine[h], src);
+        const double lc = __shfl_sync(0xffffffffu, lc_mine[h], src);
+        const double bt = __shfl_sync(0xffffffffu, bt_mine[h], src);
+        prow = sat_mul128(prow, rs);
+        pcol = sat_mul128(pcol, cs);
+        lrow += lr;
+        lcol += lc;
+        if (zero_one && rs > 1) breg += bt;
+    }
+    const unsigned __int128 b = prow < pcol ? prow : pcol;
+    const unsigned __int128 two64 = (unsigned __int128)1 << 64;
+    const unsigned __int128 maxv = ~(unsigned __int128)0;
+    if (b < two64) return kWidth64;
+    if (zero_one && breg < 63.99) return kWidth64;
+    if (b < maxv) return kWidth128;
+    if (zero_one && breg < 127.99) return kWidth128;
+    if (allow192) {
+        const double lb = lrow < lcol ? lrow : lcol;
+        if (lb < 191.99 || (zero_one && breg < 191.99)) return kWidth192;
+    }
+    return kWidthOverflow;
+}
+
 __device__ __forceinline__ int width_status(int w) {
     return w == kWidthInvalid ? PERM_EINVAL : (w == kWidthOverflow ? PERM_EOVERFLOW : PERM_OK);
 }

@@ -784,11 +784,13 @@ __global__ void ryser_finish_int(const ItemDesc* items, long long parts, int cou
     }
 }
 
-// Integer width of every matrix of a launch, once (one thread per matrix).
+// Integer width of every matrix of a launch, once (one warp per matrix).
 __global__ void ryser_widths_kernel(const long long* mats, const ItemDesc* items, int count, int n,
                                     int zero_one, int allow192, int* widths) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < count) widths[i] = decide_width(mats + items[i].offset, n, zero_one != 0, allow192 != 0);
+    const int i = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);   // uniform per warp
+    if (i >= count) return;
+    const int w = decide_width_warp(mats + items[i].offset, n, zero_one != 0, allow192 != 0);
+    if ((threadIdx.x & 31) == 0) widths[i] = w;
 }
 
 template <int N>
@@ -835,7 +837,7 @@ cudaError_t ryser_launch_group(int dtype, int n, const void* mats, const ItemDes
     if (allow192 && out_words != 4) return cudaErrorInvalidValue;
     const long long parts = parts_for(dtype, n);
     if (dtype != PERM_C128) {
-        ryser_widths_kernel<<<(count + 127) / 128, 128, 0, st>>>((const long long*)mats, items, count, n,
+        ryser_widths_kernel<<<(count + 3) / 4, 128, 0, st>>>((const long long*)mats, items, count, n,
                                                                  dtype == PERM_U01, allow192 ? 1 : 0,
                                                                  widths);
         cudaError_t e0 = cudaGetLastError();
