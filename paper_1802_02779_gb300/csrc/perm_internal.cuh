@@ -139,9 +139,11 @@ __device__ inline int decide_width(const long long* a, int n, bool zero_one, boo
 // the log2 sums) is identical to it.  The result is returned to every lane.
 __device__ inline int decide_width_warp(const long long* a, int n, bool zero_one, bool allow192) {
     const int lane = threadIdx.x & 31;
-    unsigned long long rs_mine[2] = {0ull, 0ull}, cs_mine[2] = {0ull, 0ull};
-    double lr_mine[2] = {0.0, 0.0}, bt_mine[2] = {0.0, 0.0}, lc_mine[2] = {0.0, 0.0};
+    // row / column i = lane (slot 0) and i = lane + 32 (slot 1), kept in scalars
+    unsigned long long rs0 = 0ull, rs1 = 0ull, cs0 = 0ull, cs1 = 0ull;
+    double lr0 = 0.0, lr1 = 0.0, lc0 = 0.0, lc1 = 0.0, bt0 = 0.0, bt1 = 0.0;
     bool bad = false;
+#pragma unroll
     for (int h = 0; h < 2; h++) {
         const int i = lane + 32 * h;
         if (i < n) {
@@ -152,27 +154,27 @@ __device__ inline int decide_width_warp(const long long* a, int n, bool zero_one
                 rs += (unsigned long long)v;
                 cs += (unsigned long long)a[(size_t)j * n + i];
             }
-            rs_mine[h] = rs;
-            cs_mine[h] = cs;
-            lr_mine[h] = log2((double)rs);
-            lc_mine[h] = log2((double)cs);
+            double bt = 0.0;
             if (zero_one && rs > 1) {
                 double lf = 0.0;
                 for (unsigned long long q = 2; q <= rs; q++) lf += log2((double)q);
-                bt_mine[h] = lf / (double)rs;
+                bt = lf / (double)rs;
             }
+            if (h == 0) { rs0 = rs; cs0 = cs; lr0 = log2((double)rs); lc0 = log2((double)cs); bt0 = bt; }
+            else { rs1 = rs; cs1 = cs; lr1 = log2((double)rs); lc1 = log2((double)cs); bt1 = bt; }
         }
     }
     if (__any_sync(0xffffffffu, bad)) return kWidthInvalid;
     unsigned __int128 prow = 1, pcol = 1;
     double breg = 0.0, lrow = 0.0, lcol = 0.0;
     for (int i = 0; i < n; i++) {               // row (and column) order, as decide_width
-        const int src = i & 31, h = i >> 5;
-        const unsigned long long rs = __shfl_sync(0xffffffffu, rs_mine[h], src);
-        const unsigned long long cs = __shfl_sync(0xffffffffu, cs_mine[h], src);
-        const double lr = __shfl_sync(0xffffffffu, lr_mine[h], src);
-        const double lc = __shfl_sync(0xffffffffu, lc_mine[h], src);
-        const double bt = __shfl_sync(0xffffffffu, bt_mine[h], src);
+        const int src = i & 31;
+        const bool hi = i >= 32;
+        const unsigned long long rs = __shfl_sync(0xffffffffu, hi ? rs1 : rs0, src);
+        const unsigned long long cs = __shfl_sync(0xffffffffu, hi ? cs1 : cs0, src);
+        const double lr = __shfl_sync(0xffffffffu, hi ? lr1 : lr0, src);
+        const double lc = __shfl_sync(0xffffffffu, hi ? lc1 : lc0, src);
+        const double bt = __shfl_sync(0xffffffffu, hi ? bt1 : bt0, src);
         prow = sat_mul128(prow, rs);
         pcol = sat_mul128(pcol, cs);
         lrow += lr;
