@@ -83,7 +83,7 @@ struct perm_plan_s {
     size_t stage_bytes = 0;
     cudaEvent_t stage_free = nullptr;
     unsigned* d_counter = nullptr;
-    int* d_widths = nullptr;      // integer Ryser: width per matrix of a launch
+    int* d_widths = nullptr;      // integer Ryser: width and row-sum class per matrix of a launch
 
     bool ext_ws = false;          // workspace owned by someone else (the server)
 
@@ -262,7 +262,7 @@ static perm_status plan_create_core(int n_max, perm_dtype dtype, const perm_opts
     if (e == cudaSuccess) e = cudaMalloc(&p->d_stage, p->stage_bytes);
     if (e == cudaSuccess) e = cudaMallocHost(&p->h_stage, p->stage_bytes);
     if (e == cudaSuccess) e = cudaMalloc(&p->d_counter, 64 * sizeof(unsigned));
-    if (e == cudaSuccess) e = cudaMalloc(&p->d_widths, (size_t)p->max_batch * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_widths, 2 * (size_t)p->max_batch * sizeof(int));
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->stage_free, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         cudaGetLastError();

@@ -233,7 +233,8 @@ cudaError_t sz_launch_single(int dtype, const void* mats, long long offset, int 
 
 // Ryser: every matrix's codes are cut into ryser_parts(dtype, n) CTA-sized
 // pieces (a function of n only).  One launch per distinct order n.  allow192:
-// integer widths up to 192 bits (requires out_words = 4).
+// integer widths up to 192 bits (requires out_words = 4).  widths: 2 * count
+// ints of scratch (integer types).
 long long ryser_parts(int dtype, int n);
 cudaError_t ryser_launch_group(int dtype, int n, const void* mats, const ItemDesc* items, int count,
                                void* partials, int* widths, void* out, int out_words, bool allow192,

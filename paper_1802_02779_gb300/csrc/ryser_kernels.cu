@@ -336,38 +336,41 @@ __device__ __forceinline__ void ryser_int_range(const E* __restrict__ s_col, uns
 // coefficient 2^{n-1}; every other monomial cancels).  The sum is therefore a
 // multiple of 2^{n-1}: computed modulo 2^{w+n-1} and shifted right by n-1 it
 // gives per(A) modulo 2^w exactly, over 2^{n-1} codes instead of Eq. (4)'s 2^n.
-// |rho_i| <= n, so a group of G rows with n^G < 2^31 multiplies exactly in
-// signed 32 bits; the group magnitudes multiply limb by limb modulo 2^{32 L},
-// L = ceil((w + n - 1) / 32), and the sign is applied when accumulating.
+// |rho_i| <= R_i (the row sum), so when every R_i <= B a group of G rows with
+// B^G < 2^31 multiplies exactly in signed 32 bits (B = n for 0/1 input; for
+// other integers B = 127 or 32767, chosen per matrix); the group magnitudes
+// multiply limb by limb modulo 2^{32 L}, L = ceil((w + n - 1) / 32), and the
+// sign is applied when accumulating.
 // ---------------------------------------------------------------------------
-template <int N>
+template <unsigned long long B, int N>
 constexpr int glynn_group() {
     int g = 1;
-    unsigned long long p = N;
-    while (g < N && p * N < (1ull << 31)) {
-        p *= N;
+    unsigned long long p = B;
+    while (g < N && p * B < (1ull << 31)) {
+        p *= B;
         g++;
     }
     return g;
 }
+constexpr unsigned long long kRowBound1 = 127, kRowBound2 = 32767;   // integer row-sum classes 1, 2
 
 // One thread's range of 2^log_len Glynn codes starting at g0: d_j = -1 iff bit
 // j - 1 of gray(code) is set.  s_col2[j * NP + i] = 2 a_ij, s_row[i] = sum_j a_ij.
 // log_len <= 8, and g0 is a multiple of 2^log_len, so the walk flips only the
 // low 8 bits of the Gray code (32-bit counters).
 //
-// Most terms vanish: rho_i is a sum of +-1 over the ones of row i, zero for
-// about a quarter of the sign vectors at density 1/2, so at n = 20 over 99% of
-// the products are zero.  A zero group product skips the wide product and the
-// accumulation (a branch that is uniform for most warps).  A negative term is
-// added as the complement of its magnitude, and the +1 each complement lacks
-// is added once at the end from a count.
-template <int N, int NP, int L>
-__device__ __forceinline__ void glynn_zo_range(const int* __restrict__ s_col2, const int* __restrict__ s_row,
-                                               unsigned long long g0, int log_len,
-                                               unsigned long long (&acc)[3]) {
+// For 0/1 input many terms vanish: rho_i is a sum of +-1 over the ones of row
+// i, zero for about a fifth of the sign vectors when R_i is even, so at density
+// 1/2 and n = 20 about 88% of the products are zero.  A zero group product
+// skips the wide product and the accumulation (a branch taken by a whole warp
+// only when every lane's term vanishes).  A negative term is added as the
+// complement of its magnitude, and the +1 each complement lacks is added once
+// at the end from a count.  G: rows per exact 32-bit group.
+template <int N, int NP, int L, int G>
+__device__ __forceinline__ void glynn_range(const int* __restrict__ s_col2, const int* __restrict__ s_row,
+                                            unsigned long long g0, int log_len,
+                                            unsigned long long (&acc)[3]) {
     constexpr int K = (L + 1) / 2;                 // 64-bit words of the accumulator
-    constexpr int G = glynn_group<N>();
     constexpr int kGroups = (N + G - 1) / G;
     const unsigned long long gr0 = g0 ^ (g0 >> 1);
     int r[N];
@@ -454,13 +457,13 @@ constexpr int count_planes() {
 }
 
 // The Glynn term of one code (d_j = -1 iff bit j - 1 of `code`), added to `a` as
-// described for glynn_zo_range.  s_rm[i]: bit j - 1 set iff a_ij = 1 (j >= 1).
+// described for glynn_range.  s_rm[i]: bit j - 1 set iff a_ij = 1 (j >= 1).
 template <int N, int L>
 __device__ __forceinline__ void glynn_term_from_code(unsigned code, const unsigned* __restrict__ s_rm,
                                                      const int* __restrict__ s_row,
                                                      unsigned long long (&a)[3], unsigned& ncount) {
     constexpr int K = (L + 1) / 2;
-    constexpr int G = glynn_group<N>();
+    constexpr int G = glynn_group<N, N>();
     constexpr int kGroups = (N + G - 1) / G;
     unsigned sgn = (unsigned)__popc(code) & 1u;
     int g[kGroups];
@@ -571,17 +574,25 @@ constexpr int max_width() {
     return !ZO ? 192 : (N <= 20 ? 64 : (N <= 34 ? 128 : 192));
 }
 
-template <int N, bool ZO>
-__global__ void __launch_bounds__(kRyserThreads, ZO ? 3 : 1)
+// PATH (general integers only; 0/1 matrices use kPathAll): kPathGlynn takes
+// the items with small row sums and a 64- or 128-bit width, kPathEq4 every
+// other item; the two are launched one after the other over the same pieces,
+// each writing only its own items' partial sums, so that each variant gets the
+// registers of its own arithmetic.
+enum : int { kPathAll = 0, kPathGlynn = 1, kPathEq4 = 2 };
+
+template <int N, bool ZO, int PATH>
+__global__ void __launch_bounds__(kRyserThreads, (ZO || PATH == kPathGlynn) ? 3 : 2)
 ryser_int_kernel(const long long* __restrict__ mats, const ItemDesc* __restrict__ items,
                  long long total_parts, const int* __restrict__ widths, int allow192,
                  IPartial* __restrict__ partials) {
     using E = typename std::conditional<ZO, unsigned, unsigned long long>::type;
     constexpr int NP = ZO ? ((N + 3) & ~3) : ((N + 1) & ~1);   // 16-byte columns
-    constexpr bool kEq4 = !ZO || N >= 35;                       // Eq. (4) codes needed (192 bits)
+    constexpr bool kEq4 = ZO ? N >= 35 : PATH != kPathGlynn;    // Eq. (4) codes needed
     __shared__ __align__(16) E s_col[kEq4 ? N * NP : 1];        // s_col[j * NP + i] = a_ij
-    __shared__ __align__(16) int s_col2[ZO ? N * NP : 1];       // 0/1, Glynn: 2 a_ij
-    __shared__ int s_row[ZO ? NP : 1];                          // 0/1, Glynn: sum_j a_ij
+    __shared__ __align__(16) int s_col2[N * NP];                // Glynn: 2 a_ij
+    __shared__ int s_row[NP];                                   // Glynn: sum_j a_ij
+    __shared__ int s_cls;                                       // integers: row-sum class
     constexpr bool kBits = ZO && N >= 12 && N <= 32;            // bit-sliced Glynn walk
     __shared__ unsigned s_cm[kBits ? N : 1];                    // bit i: a_ij = 1
     __shared__ unsigned s_rm[kBits ? N : 1];                    // bit j - 1: a_ij = 1 (j >= 1)
@@ -599,23 +610,38 @@ ryser_int_kernel(const long long* __restrict__ mats, const ItemDesc* __restrict_
     constexpr int kLogLenG = kLogPartG - kLogThrG;
     constexpr int kL64 = (64 + N - 1 + 31) / 32, kL128 = (128 + N - 1 + 31) / 32;
     constexpr int kMaxW = max_width<N, ZO>();
+    constexpr int kG01 = glynn_group<N, N>();                   // |rho_i| <= n
+    constexpr int kG1 = glynn_group<kRowBound1, N>(), kG2 = glynn_group<kRowBound2, N>();
+    const long long count = total_parts / kParts;               // widths[count + i]: row-sum class
 
     for (long long task = blockIdx.x; task < total_parts; task += gridDim.x) {
         const ItemDesc d = items[task / kParts];
         const long long part = task % kParts;
         const long long* a = mats + d.offset;
         __syncthreads();
+        if (threadIdx.x == 0) {
+            s_width = widths[task / kParts];
+            s_cls = ZO ? 0 : widths[count + task / kParts];
+        }
+        __syncthreads();
+        const int w = s_width;
+        // width computed: the decided one; past the bound, the widest the output holds
+        int cw = w == kWidthInvalid ? 0 : (w == kWidthOverflow ? (allow192 ? 192 : 128) : w);
+        if (cw > kMaxW) cw = kMaxW;
+        if constexpr (!ZO) {
+            const bool glynn = (cw == 64 || cw == 128) && s_cls != 0;
+            if (glynn != (PATH == kPathGlynn)) continue;     // the other launch's item (uniform)
+        }
         for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
             const int i = e / N, j = e % N;
             if constexpr (kEq4) s_col[j * NP + i] = (E)a[e];
-            if constexpr (ZO) s_col2[j * NP + i] = 2 * (int)a[e];
+            // exact whenever the Glynn walk runs (row sums <= 32767); unused otherwise
+            s_col2[j * NP + i] = (int)(unsigned)(2ull * (unsigned long long)a[e]);
         }
-        if constexpr (ZO) {
-            if (threadIdx.x < N) {
-                int rs = 0;
-                for (int j = 0; j < N; j++) rs += (int)a[threadIdx.x * N + j];
-                s_row[threadIdx.x] = rs;
-            }
+        if (threadIdx.x < N) {
+            unsigned long long rs = 0;
+            for (int j = 0; j < N; j++) rs += (unsigned long long)a[threadIdx.x * N + j];
+            s_row[threadIdx.x] = (int)(unsigned)rs;
         }
         if constexpr (kBits) {
             if (threadIdx.x < N) {
@@ -627,12 +653,7 @@ ryser_int_kernel(const long long* __restrict__ mats, const ItemDesc* __restrict_
                 s_rm[t] = rm;
             }
         }
-        if (threadIdx.x == 0) s_width = widths[task / kParts];
         __syncthreads();
-        const int w = s_width;
-        // width computed: the decided one; past the bound, the widest the output holds
-        int cw = w == kWidthInvalid ? 0 : (w == kWidthOverflow ? (allow192 ? 192 : 128) : w);
-        if (cw > kMaxW) cw = kMaxW;
         int shift = 0;                  // Glynn: the sum is 2^(n-1) per(A)
         unsigned long long acc[3] = {0ull, 0ull, 0ull};
         if constexpr (ZO) {
@@ -650,10 +671,27 @@ ryser_int_kernel(const long long* __restrict__ mats, const ItemDesc* __restrict_
                                 glynn_bits_range<N, kL128>(s_cm, s_rm, s_row, q, (unsigned)g0, kLogLenG, acc);
                         }
                     } else {
-                        if (cw == 64) glynn_zo_range<N, NP, kL64>(s_col2, s_row, g0, kLogLenG, acc);
+                        if (cw == 64) glynn_range<N, NP, kL64, kG01>(s_col2, s_row, g0, kLogLenG, acc);
                         if constexpr (kMaxW >= 128) {
-                            if (cw == 128) glynn_zo_range<N, NP, kL128>(s_col2, s_row, g0, kLogLenG, acc);
+                            if (cw == 128) glynn_range<N, NP, kL128, kG01>(s_col2, s_row, g0, kLogLenG, acc);
                         }
+                    }
+                }
+            }
+        } else if constexpr (PATH == kPathGlynn) {
+            // other integers with small row sums: the same exact Glynn walk
+            const int cls = s_cls;
+            if ((cw == 64 || cw == 128) && cls != 0) {
+                shift = N - 1;
+                if (threadIdx.x < (1 << kLogThrG)) {
+                    const unsigned long long g0 = ((unsigned long long)part << kLogPartG) +
+                                                  ((unsigned long long)threadIdx.x << kLogLenG);
+                    if (cls == 1) {
+                        if (cw == 64) glynn_range<N, NP, kL64, kG1>(s_col2, s_row, g0, kLogLenG, acc);
+                        else glynn_range<N, NP, kL128, kG1>(s_col2, s_row, g0, kLogLenG, acc);
+                    } else {
+                        if (cw == 64) glynn_range<N, NP, kL64, kG2>(s_col2, s_row, g0, kLogLenG, acc);
+                        else glynn_range<N, NP, kL128, kG2>(s_col2, s_row, g0, kLogLenG, acc);
                     }
                 }
             }
@@ -784,13 +822,31 @@ __global__ void ryser_finish_int(const ItemDesc* items, long long parts, int cou
     }
 }
 
-// Integer width of every matrix of a launch, once (one warp per matrix).
+// Integer width of every matrix of a launch, once (one warp per matrix), in
+// widths[i]; in widths[count + i] the row-sum class of the Glynn walk for
+// general integers: 1 if every row sum is <= 127, 2 if <= 32767, else 0.
 __global__ void ryser_widths_kernel(const long long* mats, const ItemDesc* items, int count, int n,
                                     int zero_one, int allow192, int* widths) {
     const int i = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);   // uniform per warp
     if (i >= count) return;
-    const int w = decide_width_warp(mats + items[i].offset, n, zero_one != 0, allow192 != 0);
-    if ((threadIdx.x & 31) == 0) widths[i] = w;
+    const long long* a = mats + items[i].offset;
+    const int w = decide_width_warp(a, n, zero_one != 0, allow192 != 0);
+    const int lane = threadIdx.x & 31;
+    unsigned long long rmax = 0ull;
+    for (int r = lane; r < n; r += 32) {
+        unsigned long long rs = 0ull;
+        for (int j = 0; j < n; j++) rs += (unsigned long long)a[(size_t)r * n + j];
+        rmax = rs > rmax ? rs : rmax;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long v = __shfl_xor_sync(0xffffffffu, rmax, o);
+        rmax = v > rmax ? v : rmax;
+    }
+    if (lane == 0) {
+        widths[i] = w;
+        widths[count + i] = rmax <= kRowBound1 ? 1 : (rmax <= kRowBound2 ? 2 : 0);
+    }
 }
 
 template <int N>
@@ -801,11 +857,13 @@ cudaError_t launch_n(int dtype, const void* mats, const ItemDesc* items, long lo
         ryser_c128_kernel<N><<<g, kRyserThreads, 0, st>>>((const double2*)mats, items, total_parts,
                                                           (CPartial*)partials);
     } else if (dtype == PERM_U01) {
-        ryser_int_kernel<N, true><<<g, kRyserThreads, 0, st>>>((const long long*)mats, items, total_parts,
-                                                               widths, allow192, (IPartial*)partials);
+        ryser_int_kernel<N, true, kPathAll><<<g, kRyserThreads, 0, st>>>(
+            (const long long*)mats, items, total_parts, widths, allow192, (IPartial*)partials);
     } else {
-        ryser_int_kernel<N, false><<<g, kRyserThreads, 0, st>>>((const long long*)mats, items, total_parts,
-                                                                widths, allow192, (IPartial*)partials);
+        ryser_int_kernel<N, false, kPathGlynn><<<g, kRyserThreads, 0, st>>>(
+            (const long long*)mats, items, total_parts, widths, allow192, (IPartial*)partials);
+        ryser_int_kernel<N, false, kPathEq4><<<g, kRyserThreads, 0, st>>>(
+            (const long long*)mats, items, total_parts, widths, allow192, (IPartial*)partials);
     }
     return cudaGetLastError();
 }
@@ -827,7 +885,7 @@ using NTable = Table<PERM_NS>;
 
 // Launch Ryser for `count` matrices that all have order n (1 <= n <= 40);
 // `partials` holds count * ryser_parts(dtype, n) 32-byte slots and `widths`
-// count ints (integer types only).
+// 2 * count ints (integer types only).
 cudaError_t ryser_launch_group(int dtype, int n, const void* mats, const ItemDesc* items, int count,
                                void* partials, int* widths, void* out, int out_words, bool allow192,
                                int* item_status, int grid, cudaStream_t st) {

@@ -189,3 +189,15 @@ def test_glynn_128_against_rook_numbers(lp, n, size, seed):
     assert 2 ** 64 < want < 2 ** 128
     res, st = lp.permanents([complement_matrix(n, cells)], "u01", return_status=True)
     assert st[0] == lp.PERM_OK and res[0] == want
+
+
+@pytest.mark.parametrize("n,hi,seed", [(7, 4, 1), (12, 4, 2), (16, 3, 3), (20, 2, 4),   # row sums <= 127
+                                       (8, 1000, 5), (10, 1000, 6),                   # <= 32767
+                                       (6, 100000, 7)])                               # Eq. 4 (larger)
+def test_small_int_glynn_classes(lp, n, hi, seed):
+    g = np.random.default_rng(seed)
+    mats = [g.integers(0, hi + 1, (n, n)).astype(np.int64) for _ in range(3)]
+    res, st = lp.permanents(mats, "i64", return_status=True)
+    assert list(st) == [lp.PERM_OK] * 3
+    assert res == [oracle.per_brute(m) if n <= 8 else oracle.per_ryser(m) for m in mats]
+    assert res == lp.permanents(mats, "i64", method=lp.METHOD_SZ)
