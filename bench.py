@@ -404,6 +404,7 @@ def measure_extras(lp, torch, cm, im, stream, c_kernel_ms, count):
             res[name + "_value"] = [float(o32[0].real), float(o32[0].imag)]
     res["sz_fp64_tflops"] = sz_c128_flops(32) / (res["store_zechin_ms"] / 1000.0) / 1e12
     out["n32"] = res
+    out["n34"] = measure_n34(lp, torch, stream)
     out["integer_methods"] = measure_integer_methods(lp, torch, im, stream, count)
     out["wide"] = measure_wide(lp, torch, stream)
     out["five_boson"] = measure_five_boson(lp, torch, stream)
@@ -419,6 +420,25 @@ def _event_ms(torch, stream, fn):
     e1.record(stream)
     torch.cuda.synchronize()
     return e0.elapsed_time(e1)
+
+
+def measure_n34(lp, torch, stream):
+    """The largest Store-zechin order, n = 34 complex: 139 GB of chain tables in HBM
+    (plan budget 150 GB), one seeded matrix of the single-instance kind, against Ryser."""
+    n = 34
+    g = np.random.default_rng(18034)
+    a = ((g.standard_normal((n, n)) + 1j * g.standard_normal((n, n))) / np.sqrt(2.0) / n).astype(np.complex128)
+    d = torch.from_numpy(a.reshape(-1)).cuda()
+    o = torch.empty(1, dtype=torch.complex128, device="cuda")
+    res = {"n": n}
+    for name, meth, budget in (("store_zechin", lp.METHOD_SZ, 150 << 30), ("ryser", lp.METHOD_RYSER, 0)):
+        with lp.Plan(n, "c128", method=meth, max_batch=1, mem_budget_bytes=budget) as p:
+            if name == "store_zechin":
+                res["workspace_gb"] = p.workspace_bytes() / 1e9
+            res[name + "_ms"] = _event_ms(torch, stream, lambda: p.batch(d, [n], o, None, stream))
+            res[name + "_value"] = [float(o[0].real), float(o[0].imag)]
+    res["sz_fp64_tflops"] = sz_c128_flops(n) / (res["store_zechin_ms"] / 1000.0) / 1e12
+    return res
 
 
 def measure_integer_methods(lp, torch, im, stream, count):
