@@ -117,10 +117,10 @@ class Clocks:
 
 
 # DRAM bytes (read + write) per n = 20 complex matrix of sz_batched_c128, from the ncu capture
-# summarised in profiles/sz_batched_c128_n20.md (304 matrices: 29.751213 GB + 7.624846 GB).
+# summarised in profiles/sz_batched_c128_n20.md (304 matrices: 29.756964 GB + 7.624674 GB).
 # Valid only for the kernel source it was measured on; otherwise the bench reports null.
-TRAFFIC_C128_PER_MATRIX = (29.751213e9 + 7.624846e9) / 304
-TRAFFIC_SOURCE_SHA256 = "4678e78db4ed3234ecf1df8ab45a9f930fb56f513d4075e0842ddf5b789a6464"
+TRAFFIC_C128_PER_MATRIX = (29.756964e9 + 7.624674e9) / 304
+TRAFFIC_SOURCE_SHA256 = "9b29e590d7fbf737089e5b1c0d3a1c802ab89d5ff44b191acce9a88ef955ceb2"
 
 
 def traffic_per_launch(count: int):
@@ -496,13 +496,13 @@ def measure_five_boson(lp, torch, stream, reps=20):
     u9 = torch.from_numpy(np.ascontiguousarray(wl.haar_unitary(9, wl.SEED_BASE + 1)[:5]).reshape(-1)).cuda()
     op = torch.empty(126, dtype=torch.complex128, device="cuda")
 
-    def timed(fn):
+    def timed(fn, st=stream):
         ts = []
         for _ in range(reps + 2):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
+            e0.record(st)
             fn()
-            e1.record(stream)
+            e1.record(st)
             torch.cuda.synchronize()
             ts.append(e0.elapsed_time(e1) * 1000.0)
         return float(np.median(ts[2:]))
@@ -512,6 +512,13 @@ def measure_five_boson(lp, torch, stream, reps=20):
         with lp.Plan(5, "c128", method=meth) as pc, lp.Plan(5, "u01", method=meth) as pi:
             res[name + "_complex_us"] = timed(lambda: pc.batch(dc, [5] * len(cm), oc, None, stream))
             res[name + "_zero_one_us"] = timed(lambda: pi.batch(di, [5] * len(im), oi, None, stream))
+        # the same calls replayed as CUDA graphs (PERM_FLAG_GRAPH, which needs a non-default
+        # stream; the graph is captured on the first call and the timing is the median after it)
+        gs = torch.cuda.Stream()
+        with lp.Plan(5, "c128", method=meth, flags=lp.FLAG_GRAPH) as pc, \
+                lp.Plan(5, "u01", method=meth, flags=lp.FLAG_GRAPH) as pi:
+            res[name + "_complex_graph_us"] = timed(lambda: pc.batch(dc, [5] * len(cm), oc, None, gs), gs)
+            res[name + "_zero_one_graph_us"] = timed(lambda: pi.batch(di, [5] * len(im), oi, None, gs), gs)
     lib = lp.load()
     res["patterns_one_pass_us"] = timed(lambda: lib.perm_patterns(
         lp._VP(u9.data_ptr()), 1, 5, 9, lp._VP(op.data_ptr()), lp._VP(stream.cuda_stream)))

@@ -319,12 +319,12 @@ namespace {
 
 // Classification of one batch: descriptors in launch order and the launch list.
 struct BatchLayout {
-    std::vector<ItemDesc> desc;      // [n = 0 items][batched Store-zechin][Ryser groups by n]
+    std::vector<ItemDesc> desc;      // [n = 0][batched Store-zechin][Store-zechin by n][Ryser by n]
     size_t triv_at = 0, ntriv = 0;
     size_t szb_at = 0, nszb = 0;
     int szb_nmax = 0;
-    std::vector<ItemDesc> szs;       // one-at-a-time Store-zechin (descriptors passed by value)
     struct Group { int n; size_t at; int cnt; };
+    std::vector<Group> szs;          // one-matrix-over-the-GPU Store-zechin, by order
     std::vector<Group> ry;
 };
 
@@ -332,6 +332,7 @@ perm_status classify(perm_plan_t p, const int* sizes, int count, BatchLayout& L)
     const bool plain = (p->flags & PERM_FLAG_PLAIN) != 0;
     std::vector<ItemDesc> triv, szb;
     std::map<int, std::vector<ItemDesc>> ry;   // by n, ascending
+    std::map<int, std::vector<ItemDesc>> szs;  // by n, ascending
     long long off = 0;
     for (int i = 0; i < count; i++) {
         const int n = sizes[i];
@@ -347,7 +348,7 @@ perm_status classify(perm_plan_t p, const int* sizes, int count, BatchLayout& L)
         }
         if (use_sz) {
             if (!plain && n <= p->sz_batch_nmax) szb.push_back(d);
-            else L.szs.push_back(d);
+            else szs[n].push_back(d);
         } else {
             ry[n].push_back(d);
         }
@@ -361,6 +362,10 @@ perm_status classify(perm_plan_t p, const int* sizes, int count, BatchLayout& L)
     L.nszb = szb.size();
     L.szb_nmax = szb.empty() ? 0 : szb.front().n;
     L.desc.insert(L.desc.end(), szb.begin(), szb.end());
+    for (auto& kv : szs) {
+        L.szs.push_back({kv.first, L.desc.size(), (int)kv.second.size()});
+        L.desc.insert(L.desc.end(), kv.second.begin(), kv.second.end());
+    }
     for (auto& kv : ry) {
         L.ry.push_back({kv.first, L.desc.size(), (int)kv.second.size()});
         L.desc.insert(L.desc.end(), kv.second.begin(), kv.second.end());
@@ -386,13 +391,22 @@ perm_status enqueue(perm_plan_t p, const BatchLayout& L, const void* mats, const
                               item_status, p->ws, p->sz_ws_per_cta, grid, p->d_counter, st);
         if (e != cudaSuccess) return PERM_ECUDA;
     }
-    for (auto& d : L.szs) {
-        // two CTAs' worth of chains per SM and layer: the per-CTA set-up is amortised, and
-        // every layer is its own launch, which gives the scheduler a point to interleave
-        // work from higher-priority streams
-        e = sz_launch_single(p->dtype, mats, d.offset, d.n, p->m_single, d.out_index, out, p->out_words,
-                             item_status, p->ws, 2 * p->num_sms, st);
-        if (e != cudaSuccess) return PERM_ECUDA;
+    for (auto& g : L.szs) {
+        // matrices of one order share every layer launch, as many as the workspace holds
+        // (one at a time when plain): the small first and last layers of one matrix leave
+        // most of the GPU idle, several fill it.  Two CTAs' worth of chains per SM and
+        // layer amortise the per-CTA set-up, and every layer is its own launch, which gives
+        // the scheduler a point to interleave work from higher-priority streams.
+        const size_t ws_item = sz_matrix_workspace_bytes(p->dtype, g.n, p->m_single);
+        long long per_launch = ws_item ? (long long)(p->ws_bytes / ws_item) : (long long)g.cnt;
+        per_launch = std::max<long long>(1, per_launch);
+        if (plain) per_launch = 1;
+        for (int b0 = 0; b0 < g.cnt; b0 += (int)per_launch) {
+            const int c = (int)std::min<long long>(per_launch, g.cnt - b0);
+            e = sz_launch_layers(p->dtype, mats, dd + g.at + b0, c, g.n, p->m_single, out, p->out_words,
+                                 item_status, p->ws, ws_item, 2 * p->num_sms, st);
+            if (e != cudaSuccess) return PERM_ECUDA;
+        }
     }
     for (auto& g : L.ry) {
         const long long parts = ryser_parts(p->dtype, g.n);

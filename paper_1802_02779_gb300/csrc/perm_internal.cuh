@@ -230,6 +230,13 @@ cudaError_t sz_launch_batched(int dtype, const void* mats, const ItemDesc* items
 cudaError_t sz_launch_single(int dtype, const void* mats, long long offset, int n, int m,
                              int out_index, void* out, int out_words, int* item_status,
                              void* workspace, int grid_cap, cudaStream_t st);
+// The same for `count` matrices of one order n (device descriptors `items`), all
+// in each layer launch; matrix c of the list uses the workspace slice
+// [c * ws_bytes_per_item, (c + 1) * ws_bytes_per_item), ws_bytes_per_item >=
+// sz_matrix_workspace_bytes(dtype, n, m).
+cudaError_t sz_launch_layers(int dtype, const void* mats, const ItemDesc* items, int count, int n, int m,
+                             void* out, int out_words, int* item_status, void* workspace,
+                             size_t ws_bytes_per_item, int grid_cap, cudaStream_t st);
 
 // Ryser: every matrix's codes are cut into ryser_parts(dtype, n) CTA-sized
 // pieces (a function of n only).  One launch per distinct order n.  allow192:

@@ -580,69 +580,97 @@ sz_batched_int(const long long* __restrict__ mats, const ItemDesc* __restrict__ 
 }
 
 // ---------------------------------------------------------------------------
-// Single-matrix kernels: one launch per layer s; CTAs stride over the slots.
+// One-matrix-at-a-time path, several matrices of one order per launch: one
+// launch per layer s, the CTAs stride over the (matrix, chain slot) pairs of
+// that layer.  Matrix c of the launch keeps its two layer regions at
+// workspace + c * ws_words_per_item.  items == nullptr: one matrix, `single`.
+// Each chain is computed exactly as in the batched kernels, so results do not
+// depend on how many matrices share a launch.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kThreadsC128Single, 1)
-sz_layer_c128(const double2* __restrict__ a, int n, int m_param, int s, double2* out, int out_index,
-              int* item_status, unsigned long long* workspace) {
+sz_layer_c128(const double2* __restrict__ mats, const ItemDesc* __restrict__ items, ItemDesc single,
+              int count, int n, int m_param, int s, double2* out, int* item_status,
+              unsigned long long* workspace, size_t ws_words_per_item) {
     extern __shared__ __align__(16) unsigned char smem[];
     fill_binom(reinterpret_cast<unsigned*>(smem));
     const SmemLayout L = smem_layout(kC128, n, sz_low_for(n, m_param));
     MatCtx mc;
     init_ctx(mc, n, m_param, smem, L);
-    load_coef_c128(a, n, smem + L.coef_off);
-    __syncthreads();
     const size_t CW = chain_words(kC128, mc.m);
     const size_t layer_words = (size_t)binom_calc(mc.t, mc.t / 2) * CW;
-    unsigned long long* dst_region = workspace + (size_t)(s & 1) * layer_words;
-    const unsigned long long* src_region = workspace + (size_t)((s + 1) & 1) * layer_words;
     const unsigned nslots = (unsigned)binom_calc(mc.t, s);
     const bool last = (s == mc.t);
-    for (unsigned slot = blockIdx.x; slot < nslots; slot += gridDim.x) {
+    const long long tasks = (long long)count * nslots;
+    int cur = -1;
+    for (long long task = blockIdx.x; task < tasks; task += gridDim.x) {
+        const int c = (int)(task / nslots);
+        const unsigned slot = (unsigned)(task % nslots);
+        const ItemDesc d = items ? items[c] : single;
+        if (c != cur) {                 // the same for the whole CTA
+            __syncthreads();
+            load_coef_c128(mats + d.offset, n, smem + L.coef_off);
+            cur = c;
+        }
+        unsigned long long* ws = workspace + (size_t)c * ws_words_per_item;
+        unsigned long long* dst_region = ws + (size_t)(s & 1) * layer_words;
+        const unsigned long long* src_region = ws + (size_t)((s + 1) & 1) * layer_words;
         chain_setup(mc, unrank_high(slot, s, mc.t, mc.bn), reinterpret_cast<int*>(smem + L.hinfo_off));
         __syncthreads();
         run_chain<kC128, false>(mc, s, smem + L.chain_off, src_region,
                                 last ? nullptr : dst_region + (size_t)slot * CW, smem + L.coef_off,
-                                last, out, out_index);
+                                last, out, d.out_index);
+        if (last && threadIdx.x == 0 && item_status) item_status[d.out_index] = PERM_OK;
     }
-    if (last && blockIdx.x == 0 && threadIdx.x == 0 && item_status) item_status[out_index] = PERM_OK;
 }
 
 template <bool ZO>
 __global__ void __launch_bounds__(kThreadsInt, 3)
-sz_layer_int(const long long* __restrict__ a, int n, int m_param, int s, unsigned long long* out,
-             int out_words, int out_index, int* item_status, unsigned long long* workspace) {
+sz_layer_int(const long long* __restrict__ mats, const ItemDesc* __restrict__ items, ItemDesc single,
+             int count, int n, int m_param, int s, unsigned long long* out, int out_words,
+             int* item_status, unsigned long long* workspace, size_t ws_words_per_item) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_width;
     fill_binom(reinterpret_cast<unsigned*>(smem));
-    if (threadIdx.x == 0) s_width = decide_width(a, n, ZO);
     const SmemLayout L = smem_layout(kU128, n, sz_low_for(n, m_param));
     MatCtx mc;
     init_ctx(mc, n, m_param, smem, L);
     mc.out_words = out_words;
-    load_coef_int(a, n, mc.m, reinterpret_cast<unsigned long long*>(smem + L.coef_off),
-                  reinterpret_cast<unsigned*>(smem + L.rowmask_off));
-    __syncthreads();
-    const int w = s_width;
-    const int kind = (w == kWidth64) ? kU64 : kU128;
-    const size_t CW = chain_words(kind, mc.m);
     // the workspace is sized for 128-bit chains; 64-bit chains use the same region size
     const size_t layer_words = (size_t)binom_calc(mc.t, mc.t / 2) * chain_words(kU128, mc.m);
-    unsigned long long* dst_region = workspace + (size_t)(s & 1) * layer_words;
-    const unsigned long long* src_region = workspace + (size_t)((s + 1) & 1) * layer_words;
     const unsigned nslots = (unsigned)binom_calc(mc.t, s);
     const bool last = (s == mc.t);
-    for (unsigned slot = blockIdx.x; slot < nslots; slot += gridDim.x) {
+    const long long tasks = (long long)count * nslots;
+    int cur = -1;
+    for (long long task = blockIdx.x; task < tasks; task += gridDim.x) {
+        const int c = (int)(task / nslots);
+        const unsigned slot = (unsigned)(task % nslots);
+        const ItemDesc d = items ? items[c] : single;
+        if (c != cur) {                 // the same for the whole CTA
+            __syncthreads();
+            const long long* a = mats + d.offset;
+            if (threadIdx.x == 0) s_width = decide_width(a, n, ZO);
+            load_coef_int(a, n, mc.m, reinterpret_cast<unsigned long long*>(smem + L.coef_off),
+                          reinterpret_cast<unsigned*>(smem + L.rowmask_off));
+            cur = c;
+        }
+        __syncthreads();
+        const int w = s_width;
+        const int kind = (w == kWidth64) ? kU64 : kU128;
+        const size_t CW = chain_words(kind, mc.m);
+        unsigned long long* ws = workspace + (size_t)c * ws_words_per_item;
+        unsigned long long* dst_region = ws + (size_t)(s & 1) * layer_words;
+        const unsigned long long* src_region = ws + (size_t)((s + 1) & 1) * layer_words;
         chain_setup(mc, unrank_high(slot, s, mc.t, mc.bn), reinterpret_cast<int*>(smem + L.hinfo_off));
         __syncthreads();
         unsigned long long* dst = last ? nullptr : dst_region + (size_t)slot * CW;
         if (kind == kU64)
-            run_chain<kU64, ZO>(mc, s, smem + L.chain_off, src_region, dst, smem + L.coef_off, last, out, out_index);
+            run_chain<kU64, ZO>(mc, s, smem + L.chain_off, src_region, dst, smem + L.coef_off, last, out,
+                                d.out_index);
         else
-            run_chain<kU128, ZO>(mc, s, smem + L.chain_off, src_region, dst, smem + L.coef_off, last, out, out_index);
+            run_chain<kU128, ZO>(mc, s, smem + L.chain_off, src_region, dst, smem + L.coef_off, last, out,
+                                 d.out_index);
+        if (last && threadIdx.x == 0 && item_status) item_status[d.out_index] = width_status(w);
     }
-    if (last && blockIdx.x == 0 && threadIdx.x == 0 && item_status)
-        item_status[out_index] = width_status(w);
 }
 
 __global__ void trivial_kernel(int dtype, const ItemDesc* items, int count, void* out, int out_words,
@@ -790,9 +818,15 @@ cudaError_t sz_launch_batched(int dtype, const void* mats, const ItemDesc* items
     return cudaGetLastError();
 }
 
-cudaError_t sz_launch_single(int dtype, const void* mats, long long offset, int n, int m,
-                             int out_index, void* out, int out_words, int* item_status,
-                             void* workspace, int grid_cap, cudaStream_t st) {
+namespace {
+
+// Layers 0..t of `count` matrices of order n (items on the device, or one
+// matrix `single` when items == nullptr).
+cudaError_t sz_launch_layers_impl(int dtype, const void* mats, const ItemDesc* items, ItemDesc single,
+                                  int count, int n, int m, void* out, int out_words, int* item_status,
+                                  void* workspace, size_t ws_bytes_per_item, int grid_cap,
+                                  cudaStream_t st) {
+    if (count <= 0) return cudaSuccess;
     const int mm = sz_low_for(n, m);
     const int t = n - mm;
     const int smem = sz_smem_bytes(dtype, n, m);
@@ -800,25 +834,43 @@ cudaError_t sz_launch_single(int dtype, const void* mats, long long offset, int 
                    : (dtype == PERM_U01 ? (const void*)sz_layer_int<true> : (const void*)sz_layer_int<false>);
     cudaError_t e = set_smem(fn, smem);
     if (e != cudaSuccess) return e;
+    const size_t wpi = ws_bytes_per_item / 8;
     for (int s = 0; s <= t; s++) {
-        const int grid = (int)std::min<unsigned long long>(binom_calc(t, s), (unsigned long long)grid_cap);
+        const unsigned long long tasks = binom_calc(t, s) * (unsigned long long)count;
+        const int grid = (int)std::min<unsigned long long>(tasks, (unsigned long long)grid_cap);
         if (dtype == PERM_C128) {
             sz_layer_c128<<<grid, kThreadsC128Single, smem, st>>>(
-                (const double2*)mats + offset, n, m, s, (double2*)out, out_index, item_status,
-                (unsigned long long*)workspace);
+                (const double2*)mats, items, single, count, n, m, s, (double2*)out, item_status,
+                (unsigned long long*)workspace, wpi);
         } else if (dtype == PERM_U01) {
             sz_layer_int<true><<<grid, kThreadsInt, smem, st>>>(
-                (const long long*)mats + offset, n, m, s, (unsigned long long*)out, out_words,
-                out_index, item_status, (unsigned long long*)workspace);
+                (const long long*)mats, items, single, count, n, m, s, (unsigned long long*)out, out_words,
+                item_status, (unsigned long long*)workspace, wpi);
         } else {
             sz_layer_int<false><<<grid, kThreadsInt, smem, st>>>(
-                (const long long*)mats + offset, n, m, s, (unsigned long long*)out, out_words,
-                out_index, item_status, (unsigned long long*)workspace);
+                (const long long*)mats, items, single, count, n, m, s, (unsigned long long*)out, out_words,
+                item_status, (unsigned long long*)workspace, wpi);
         }
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t sz_launch_layers(int dtype, const void* mats, const ItemDesc* items, int count, int n, int m,
+                             void* out, int out_words, int* item_status, void* workspace,
+                             size_t ws_bytes_per_item, int grid_cap, cudaStream_t st) {
+    return sz_launch_layers_impl(dtype, mats, items, ItemDesc{0, n, 0}, count, n, m, out, out_words,
+                                 item_status, workspace, ws_bytes_per_item, grid_cap, st);
+}
+
+cudaError_t sz_launch_single(int dtype, const void* mats, long long offset, int n, int m,
+                             int out_index, void* out, int out_words, int* item_status,
+                             void* workspace, int grid_cap, cudaStream_t st) {
+    return sz_launch_layers_impl(dtype, mats, nullptr, ItemDesc{offset, n, out_index}, 1, n, m, out,
+                                 out_words, item_status, workspace, 0, grid_cap, st);
 }
 
 cudaError_t launch_trivial(int dtype, const ItemDesc* items, int count, void* out, int out_words,
