@@ -347,7 +347,7 @@ def run_gpu(args, rank, world):
                                   "zero_one": ("Store-zechin batched integer kernel (--int-method sz)"
                                                if args.int_method == "sz" else
                                                "Ryser Gray-code kernel (PERM_METHOD_AUTO's method for integers): "
-                                               "width kernel, one CTA per 2^17 codes, finishing kernel")},
+                                               "width kernel, one CTA per 2^16 Glynn codes, finishing kernel")},
                        "l2": "flushed between timed steps (256 MB write)",
                        "plans": {"complex128": pc.describe(), "zero_one": pi.describe()},
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
@@ -584,29 +584,79 @@ def measure_serving(lp, arrival_window_s=60.0, drain_s=120.0):
         arrivals = arrivals[arrivals < arrival_window_s]
         reqs = pool[:len(arrivals)]
         pending = {}
-        lat = []
+        lat, lat_n = [], []
         start = time.perf_counter()
         i = 0
         while i < len(reqs) or pending:
             now = time.perf_counter() - start
             while i < len(reqs) and arrivals[i] <= now:
-                pending[srv.submit(reqs[i].mat, reqs[i].dtype)] = arrivals[i]
+                pending[srv.submit(reqs[i].mat, reqs[i].dtype)] = (arrivals[i], reqs[i].n)
                 i += 1
             for t in list(pending):
                 state, _ = srv.poll(t)
                 if state == "done":
-                    lat.append(time.perf_counter() - start - pending.pop(t))
+                    t_arr, n_req = pending.pop(t)
+                    lat.append(time.perf_counter() - start - t_arr)
+                    lat_n.append(n_req)
             if now > arrival_window_s + drain_s:
                 break
             time.sleep(0.0005)
         elapsed = time.perf_counter() - start
     lat = np.array(lat)
+    plain = serve_plain(lp, reqs, arrivals, arrival_window_s + drain_s)
     return {"arrival_rate_per_s": rate, "capacity_per_s": capacity, "requests": int(len(reqs)),
             "completed": int(len(lat)), "p50_ms": float(np.percentile(lat, 50) * 1e3) if len(lat) else None,
             "p99_ms": float(np.percentile(lat, 99) * 1e3) if len(lat) else None,
             "perm_per_s": float(len(lat) / elapsed), "n_range": [10, 36],
+            **latency_split(lat, np.array(lat_n)),
             "calibration": "one complex request of each n = 10..36 served back to back",
-            "table_budget": "server default (min(80 GB, free/3))"}
+            "table_budget": "server default (min(80 GB, free/3))",
+            "plain": plain}
+
+
+def latency_split(lat, ns):
+    """p90 of all requests, and p50/p99 of the small (n <= 20) and large requests apart."""
+    out = {"p90_ms": float(np.percentile(lat, 90) * 1e3) if len(lat) else None}
+    for name, sel in (("small_n_le_20", ns <= 20), ("large", ns > 20)):
+        x = lat[sel]
+        out[name] = {"count": int(len(x)),
+                     "p50_ms": float(np.percentile(x, 50) * 1e3) if len(x) else None,
+                     "p99_ms": float(np.percentile(x, 99) * 1e3) if len(x) else None}
+    return out
+
+
+def serve_plain(lp, reqs, arrivals, limit_s):
+    """The same arrival trace served by plain per-request launches: one blocking
+    perm_batch_host call per request in arrival order (PERM_FLAG_PLAIN plans,
+    the default method choice), latency = completion minus scheduled arrival."""
+    plans = {dt: lp.Plan(36, dt, flags=lp.FLAG_PLAIN, max_batch=1) for dt in ("c128", "u01")}
+    out_c = np.zeros(2, dtype=np.float64)
+    out_i = np.zeros(2, dtype=np.int64)
+    st = np.zeros(1, dtype=np.int32)
+    lat, lat_n = [], []
+    try:
+        start = time.perf_counter()
+        for r, t_arr in zip(reqs, arrivals):
+            now = time.perf_counter() - start
+            if t_arr > now:
+                time.sleep(t_arr - now)
+            a = np.ascontiguousarray(r.mat, dtype=np.complex128 if r.dtype == "c128" else np.int64)
+            plans[r.dtype].batch_host(a.reshape(-1), [a.shape[0]], out_c if r.dtype == "c128" else out_i, st)
+            lat.append(time.perf_counter() - start - t_arr)
+            lat_n.append(r.n)
+            if time.perf_counter() - start > limit_s:
+                break
+        elapsed = time.perf_counter() - start
+    finally:
+        for p in plans.values():
+            p.close()
+    lat = np.array(lat)
+    return {"completed": int(len(lat)),
+            "p50_ms": float(np.percentile(lat, 50) * 1e3) if len(lat) else None,
+            "p99_ms": float(np.percentile(lat, 99) * 1e3) if len(lat) else None,
+            "perm_per_s": float(len(lat) / elapsed) if len(lat) else 0.0,
+            **latency_split(lat, np.array(lat_n)),
+            "how": "one blocking perm_batch_host call per request in arrival order, PERM_FLAG_PLAIN"}
 
 
 def run_single(args):

@@ -236,6 +236,13 @@ static perm_status plan_create_core(int n_max, perm_dtype dtype, const perm_opts
     }
     p->ws_bytes = std::max(sz_batched, sz_single);
 
+    // load every kernel this plan can launch now, not at its first launch
+    if ((uses_sz && sz_preload(dtype) != cudaSuccess) || ryser_preload(dtype, n_max) != cudaSuccess) {
+        cudaGetLastError();
+        delete p;
+        return PERM_ECUDA;
+    }
+
     // ---- Ryser partials (32 B per piece of 2^17 codes): one matrix of the largest order,
     // max_batch matrices of one piece each, and up to 2^20 pieces (32 MB) so that a batch of
     // mid-size matrices fills the GPU in one launch instead of many small ones ----
@@ -352,6 +359,14 @@ perm_status classify(perm_plan_t p, const int* sizes, int count, BatchLayout& L)
         } else {
             ry[n].push_back(d);
         }
+    }
+    // With fewer such matrices than SMs, one CTA per matrix would leave most of the GPU idle
+    // (and one n = 20 matrix takes ~20 ms on one CTA): the layer path spreads every matrix's
+    // chains over the whole GPU instead.  Both paths sum every entry in the same order, so
+    // the results are the same bits.
+    if (!plain && (int)szb.size() < p->num_sms) {
+        for (auto& d : szb) szs[d.n].push_back(d);
+        szb.clear();
     }
     // longest matrices first for the persistent queue
     std::stable_sort(szb.begin(), szb.end(), [](const ItemDesc& a, const ItemDesc& b) { return a.n > b.n; });

@@ -247,6 +247,13 @@ cudaError_t ryser_launch_group(int dtype, int n, const void* mats, const ItemDes
                                void* partials, int* widths, void* out, int out_words, bool allow192,
                                int* item_status, int grid, cudaStream_t st);
 
+// Load now every kernel a plan of this element type may launch (Ryser: orders
+// 1..n_max).  The runtime otherwise loads a kernel at its first launch, and
+// that load can wait for all work running on the device -- which would stall a
+// thread that feeds several streams (the server).
+cudaError_t sz_preload(int dtype);
+cudaError_t ryser_preload(int dtype, int n_max);
+
 // n = 0 items: per = 1.
 cudaError_t launch_trivial(int dtype, const ItemDesc* items, int count, void* out, int out_words,
                            int* item_status, cudaStream_t st);

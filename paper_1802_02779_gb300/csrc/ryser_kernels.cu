@@ -14,7 +14,8 @@
 // integer path cannot use it because 2^{-(n-1)} does not exist modulo 2^w).
 //
 // Work split.  The 2^G codes of one matrix are cut into `parts` CTA-sized
-// pieces of 2^17 codes (one piece when there are fewer), each piece into 256
+// pieces of 2^17 codes (2^16 for complex input; one piece when there are
+// fewer), each piece into 256
 // contiguous thread ranges.  The grid has one CTA per piece, so CTAs retire
 // every few milliseconds and work on higher-priority streams can take their
 // place.  A thread computes its first row sums directly
@@ -34,14 +35,19 @@ namespace perm {
 namespace {
 
 constexpr int kRyserThreads = 256;
-constexpr int kLogCodesPerPart = 17;   // one CTA covers 2^17 codes, then retires
+// One CTA covers 2^17 integer codes (2^16 for complex input, whose codes cost
+// about 6n FP64 operations each: a CTA then runs ~3.5 ms at n = 34), then
+// retires, so work on a higher-priority stream waits at most that long for SMs.
+constexpr int kLogCodesPerPart = 17;
+constexpr int kLogCodesPerPartC = 16;
 
 __host__ __device__ inline int log_codes(int dtype, int n) {
     return dtype == PERM_C128 ? n - 1 : n;
 }
 __host__ __device__ inline long long parts_for(int dtype, int n) {
     const int lg = log_codes(dtype, n);
-    return lg > kLogCodesPerPart ? (1ll << (lg - kLogCodesPerPart)) : 1ll;
+    const int per = dtype == PERM_C128 ? kLogCodesPerPartC : kLogCodesPerPart;
+    return lg > per ? (1ll << (lg - per)) : 1ll;
 }
 
 struct CPartial { double re_hi, re_lo, im_hi, im_lo; };
@@ -61,8 +67,8 @@ ryser_c128_kernel(const double2* __restrict__ mats, const ItemDesc* __restrict__
     __shared__ double2 s_row0[N > 0 ? N : 1];                  // full row sums sum_j a_ij (d = +1)
     __shared__ dd2 s_re[kRyserThreads], s_im[kRyserThreads];
     constexpr int G = N - 1;                                    // log2 of the code count
-    constexpr long long kParts = (G > kLogCodesPerPart) ? (1ll << (G - kLogCodesPerPart)) : 1ll;
-    constexpr int kLogPart = (G > kLogCodesPerPart) ? kLogCodesPerPart : G;
+    constexpr long long kParts = (G > kLogCodesPerPartC) ? (1ll << (G - kLogCodesPerPartC)) : 1ll;
+    constexpr int kLogPart = (G > kLogCodesPerPartC) ? kLogCodesPerPartC : G;
     constexpr int kLogThr = kLogPart >= 8 ? 8 : kLogPart;       // threads actually used = 2^kLogThr
     constexpr int kLogLen = kLogPart - kLogThr;                 // codes per thread = 2^kLogLen
 
@@ -871,9 +877,29 @@ cudaError_t launch_n(int dtype, const void* mats, const ItemDesc* items, long lo
 typedef cudaError_t (*launch_fn)(int, const void*, const ItemDesc*, long long, const int*, int, void*,
                                  int, cudaStream_t);
 
+// Load the kernels of order N for `dtype` now (cudaFuncGetAttributes makes the
+// runtime load a function): a lazy load at the first launch can wait for every
+// kernel running on the device, which would stall a serving thread.
+template <int N>
+cudaError_t preload_n(int dtype) {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaSuccess;
+    if (dtype == PERM_C128) {
+        e = cudaFuncGetAttributes(&fa, (const void*)ryser_c128_kernel<N>);
+    } else if (dtype == PERM_U01) {
+        e = cudaFuncGetAttributes(&fa, (const void*)ryser_int_kernel<N, true, kPathAll>);
+    } else {
+        e = cudaFuncGetAttributes(&fa, (const void*)ryser_int_kernel<N, false, kPathGlynn>);
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, (const void*)ryser_int_kernel<N, false, kPathEq4>);
+    }
+    return e;
+}
+typedef cudaError_t (*preload_fn)(int);
+
 template <int... Ns>
 struct Table {
     static constexpr launch_fn fns[sizeof...(Ns)] = {&launch_n<Ns>...};
+    static constexpr preload_fn pre[sizeof...(Ns)] = {&preload_n<Ns>...};
 };
 
 #define PERM_NS 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19, 20, 21, 22, 23, \
@@ -914,5 +940,14 @@ cudaError_t ryser_launch_group(int dtype, int n, const void* mats, const ItemDes
 }
 
 long long ryser_parts(int dtype, int n) { return parts_for(dtype, n); }
+
+cudaError_t ryser_preload(int dtype, int n_max) {
+    cudaFuncAttributes fa;
+    cudaError_t e = dtype == PERM_C128 ? cudaFuncGetAttributes(&fa, (const void*)ryser_finish_c128)
+                                       : cudaFuncGetAttributes(&fa, (const void*)ryser_finish_int);
+    if (e == cudaSuccess && dtype != PERM_C128) e = cudaFuncGetAttributes(&fa, (const void*)ryser_widths_kernel);
+    for (int n = 1; n <= std::min(n_max, kMaxN) && e == cudaSuccess; n++) e = NTable::pre[n - 1](dtype);
+    return e;
+}
 
 }  // namespace perm

@@ -345,6 +345,13 @@ perm_status perm_server_create(const perm_opts* opts, void* stream, perm_server_
         large.ext_ws_bytes = s->table_budget;
         ok = cudaMalloc(&large.ext_ws, large.ext_ws_bytes) == cudaSuccess;
     }
+    // every lane's plans now (they load their kernels): creating one, or loading a kernel,
+    // while another lane's work runs could wait for that work
+    for (int dt : {PERM_C128, PERM_U01, PERM_I64}) {
+        if (ok) ok = lane_plan(s, small, dt, false) != nullptr;
+        if (ok) ok = lane_plan(s, ryser, dt, true) != nullptr;
+    }
+    if (ok) ok = lane_plan(s, large, PERM_C128, true) != nullptr;   // the table lane takes complex requests
     if (!ok) {
         cudaGetLastError();
         for (auto& L : s->lanes) lane_free(L);

@@ -708,8 +708,27 @@ int batched_kind(int dtype, int n_max) {
     return (dtype == PERM_U01 && n_max <= 20) ? kU64 : kU128;
 }
 
+// Allow `fn` the largest dynamic shared memory the device offers, once per
+// (device, kernel), so that launches on the hot path make no attribute call.
 cudaError_t set_smem(const void* fn, int bytes) {
-    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    static std::mutex mu;
+    static std::vector<std::pair<int, const void*>> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> g(mu);
+    for (auto& d : done)
+        if (d.first == dev && d.second == fn) return cudaSuccess;
+    int optin = 0;
+    cudaFuncAttributes fa;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess) return e;
+    const int dyn = optin - (int)fa.sharedSizeBytes;
+    if (bytes > dyn) return cudaErrorInvalidValue;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+    if (e == cudaSuccess) done.emplace_back(dev, fn);
+    return e;
 }
 
 }  // namespace
@@ -871,6 +890,28 @@ cudaError_t sz_launch_single(int dtype, const void* mats, long long offset, int 
                              void* workspace, int grid_cap, cudaStream_t st) {
     return sz_launch_layers_impl(dtype, mats, nullptr, ItemDesc{offset, n, out_index}, 1, n, m, out,
                                  out_words, item_status, workspace, 0, grid_cap, st);
+}
+
+cudaError_t sz_preload(int dtype) {
+    cudaFuncAttributes fa;
+    const void* fns[8];
+    int k = 0;
+    fns[k++] = (const void*)trivial_kernel;
+    if (dtype == PERM_C128) {
+        fns[k++] = c128_batched_fn(256);
+        fns[k++] = c128_batched_fn(384);
+        fns[k++] = c128_batched_fn(512);
+        fns[k++] = (const void*)sz_layer_c128;
+    } else {
+        for (int n_max : {20, 34})
+            for (int threads : {256, 512}) fns[k++] = (const void*)pick_int_batched(dtype, n_max, threads);
+        fns[k++] = dtype == PERM_U01 ? (const void*)sz_layer_int<true> : (const void*)sz_layer_int<false>;
+    }
+    for (int i = 0; i < k; i++) {
+        const cudaError_t e = cudaFuncGetAttributes(&fa, fns[i]);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_trivial(int dtype, const ItemDesc* items, int count, void* out, int out_words,
