@@ -146,6 +146,21 @@ def test_alone_vs_mix_bitwise(lp):
     assert list(plain) == list(mixed)
 
 
+def test_batched_kernel_and_layer_path_same_bits(lp):
+    """A call with at least as many Store-zechin matrices as SMs runs the batched
+    kernel (one CTA per matrix, chain width 12); one matrix alone runs the layer
+    path (the chains of each layer over the whole GPU, chain width 13).  Every
+    entry is summed over its columns in ascending order on both, so the bits agree."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    ns = [16, 20, 9, 13, 18] * ((sms + 4) // 5 + 1)
+    mats = [rand_complex(n, 9300 + i) for i, n in enumerate(ns)]
+    batched = lp.permanents(mats, "c128")
+    for i in range(0, len(mats), 37):          # a sample, one matrix per call
+        assert lp.permanents([mats[i]], "c128")[0] == batched[i]
+    for i in (0, 1, 4):
+        assert abs(batched[i] - oracle_c(mats[i])) <= tol_c(mats[i])
+
+
 def test_sz_and_ryser_agree_n24(lp):
     m = rand_complex(24, 99)
     a = lp.permanents([m], "c128", method=lp.METHOD_SZ)[0]
