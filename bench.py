@@ -117,10 +117,10 @@ class Clocks:
 
 
 # DRAM bytes (read + write) per n = 20 complex matrix of sz_batched_c128, from the ncu capture
-# summarised in profiles/sz_batched_c128_n20.md (304 matrices: 29.756964 GB + 7.624674 GB).
+# summarised in profiles/sz_batched_c128_n20.md (304 matrices: 29.750804 GB + 7.624042 GB).
 # Valid only for the kernel source it was measured on; otherwise the bench reports null.
-TRAFFIC_C128_PER_MATRIX = (29.756964e9 + 7.624674e9) / 304
-TRAFFIC_SOURCE_SHA256 = "9b29e590d7fbf737089e5b1c0d3a1c802ab89d5ff44b191acce9a88ef955ceb2"
+TRAFFIC_C128_PER_MATRIX = (29.750804e9 + 7.624042e9) / 304
+TRAFFIC_SOURCE_SHA256 = "17218d88051d3fc3f36347bb314cab34644d32f4458a3342f0998d6725150261"
 
 
 def traffic_per_launch(count: int):
