@@ -70,3 +70,39 @@ def test_library_is_built_for_sm103a():
     """The build passes exactly one -gencode for sm_103a."""
     from paper_1802_02779_gb300 import build
     assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def header_constants():
+    """Every `PERM_X = v` enumerator and `#define PERM_FLAG_X v` of the header."""
+    text = open(HEADER).read()
+    consts = {k: int(v) for k, v in re.findall(r"\b(PERM_[A-Z0-9_]+)\s*=\s*(\d+)", text)}
+    consts.update({k: int(v) for k, v in re.findall(r"#define\s+(PERM_FLAG_[A-Z0-9_]+)\s+(\d+)u", text)})
+    return consts
+
+
+def test_binding_constants_match_the_header():
+    from paper_1802_02779_gb300 import libperm as lp
+    c = header_constants()
+    binding = {
+        "PERM_OK": lp.PERM_OK, "PERM_EINVAL": lp.PERM_EINVAL, "PERM_ENOMEM": lp.PERM_ENOMEM,
+        "PERM_EOVERFLOW": lp.PERM_EOVERFLOW, "PERM_ECUDA": lp.PERM_ECUDA, "PERM_EAGAIN": lp.PERM_EAGAIN,
+        "PERM_ETIMEDOUT": lp.PERM_ETIMEDOUT, "PERM_ESHUTDOWN": lp.PERM_ESHUTDOWN,
+        "PERM_ENOTFOUND": lp.PERM_ENOTFOUND,
+        "PERM_C128": lp.PERM_C128, "PERM_U01": lp.PERM_U01, "PERM_I64": lp.PERM_I64,
+        "PERM_METHOD_AUTO": lp.METHOD_AUTO, "PERM_METHOD_SZ": lp.METHOD_SZ, "PERM_METHOD_RYSER": lp.METHOD_RYSER,
+        "PERM_FLAG_PLAIN": lp.FLAG_PLAIN, "PERM_FLAG_GRAPH": lp.FLAG_GRAPH,
+        "PERM_FLAG_AUTOTUNE": lp.FLAG_AUTOTUNE, "PERM_FLAG_WIDE": lp.FLAG_WIDE,
+    }
+    assert set(binding) == set(c)
+    for k, v in binding.items():
+        assert c[k] == v, k
+
+
+def test_opts_struct_matches_the_header():
+    """perm_opts: the ctypes fields are the header's fields, in order, with the same C types."""
+    from paper_1802_02779_gb300 import libperm as lp
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    body = re.search(r"typedef struct perm_opts\s*\{(.*?)\}\s*perm_opts;", text, re.S).group(1)
+    fields = re.findall(r"(size_t|int|unsigned)\s+([a-z_]+)\s*;", body)
+    ctypes_of = {"size_t": ctypes.c_size_t, "int": ctypes.c_int, "unsigned": ctypes.c_uint}
+    assert [(n, ctypes_of[t]) for t, n in fields] == list(lp.PermOpts._fields_)
