@@ -243,15 +243,15 @@ static perm_status plan_create_core(int n_max, perm_dtype dtype, const perm_opts
         return PERM_ECUDA;
     }
 
-    // ---- Ryser partials (32 B per piece of 2^17 codes): one matrix of the largest order,
-    // max_batch matrices of one piece each, and up to 2^20 pieces (32 MB) so that a batch of
-    // mid-size matrices fills the GPU in one launch instead of many small ones ----
+    // ---- Ryser partials (32-40 B per piece of codes): one matrix of the largest order,
+    // max_batch matrices of one piece each, and up to 2^20 pieces (32-40 MB) so that a batch
+    // of mid-size matrices fills the GPU in one launch instead of many small ones ----
     long long max_parts = 1;
     for (int n = 1; n <= n_max; n++) max_parts = std::max(max_parts, ryser_parts(dtype, n));
     long long cap = std::max<long long>(max_parts, (long long)p->max_batch);
     cap = std::max<long long>(cap, std::min<long long>(max_parts * (long long)p->max_batch, 1ll << 20));
     p->partials_cap = cap;
-    p->partials_bytes = (size_t)cap * 32;
+    p->partials_bytes = (size_t)cap * ryser_partial_bytes(dtype);
 
     // ---- descriptor staging ----
     const int mb = p->max_batch;

@@ -243,6 +243,7 @@ cudaError_t sz_launch_layers(int dtype, const void* mats, const ItemDesc* items,
 // integer widths up to 192 bits (requires out_words = 4).  widths: 2 * count
 // ints of scratch (integer types).
 long long ryser_parts(int dtype, int n);
+size_t ryser_partial_bytes(int dtype);                   // bytes of one piece's partial sum
 cudaError_t ryser_launch_group(int dtype, int n, const void* mats, const ItemDesc* items, int count,
                                void* partials, int* widths, void* out, int out_words, bool allow192,
                                int* item_status, int grid, cudaStream_t st);

@@ -54,7 +54,7 @@ struct CPartial { double re_hi, re_lo, im_hi, im_lo; };
 // meta: item status in bits 0..31, the width computed (0, 64, 128, 192) in bits
 // 32..47, and the right shift the finished sum needs (n - 1 for Glynn's form,
 // else 0) in bits 48..55
-struct IPartial { unsigned long long w0, w1, w2, meta; };
+struct IPartial { unsigned long long w[4], meta; };
 
 // ---------------------------------------------------------------------------
 // Complex (Glynn), compile-time order N.
@@ -179,21 +179,33 @@ __device__ __forceinline__ U128 u128_mul(U128 a, U128 b) {
     return {a.lo * b.lo, __umul64hi(a.lo, b.lo) + a.lo * b.hi + a.hi * b.lo};
 }
 
-// acc += x / acc -= x over the low K words (K = 1, 2, 3), carries propagated.
-template <int K>
-__device__ __forceinline__ void words_add(unsigned long long (&acc)[3], const unsigned long long (&x)[3]) {
+// Integer accumulators: up to four 64-bit words (Glynn's sum modulo 2^(192+n-1)
+// needs four at n >= 34).
+constexpr int kAccWords = 4;
+typedef unsigned long long AccWords[kAccWords];
+
+// acc += x / acc -= x over the low K words (K = 1..4), carries propagated.
+template <int K, int NA, int NX>
+__device__ __forceinline__ void words_add(unsigned long long (&acc)[NA], const unsigned long long (&x)[NX]) {
+    static_assert(K <= NA && K <= NX, "word count");
     if constexpr (K == 1) {
         acc[0] += x[0];
     } else if constexpr (K == 2) {
         asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, %3;"
             : "+l"(acc[0]), "+l"(acc[1]) : "l"(x[0]), "l"(x[1]));
-    } else {
+    } else if constexpr (K == 3) {
         asm("add.cc.u64 %0, %0, %3;\n\taddc.cc.u64 %1, %1, %4;\n\taddc.u64 %2, %2, %5;"
             : "+l"(acc[0]), "+l"(acc[1]), "+l"(acc[2]) : "l"(x[0]), "l"(x[1]), "l"(x[2]));
+    } else {
+        asm("add.cc.u64 %0, %0, %4;\n\taddc.cc.u64 %1, %1, %5;\n\taddc.cc.u64 %2, %2, %6;\n\t"
+            "addc.u64 %3, %3, %7;"
+            : "+l"(acc[0]), "+l"(acc[1]), "+l"(acc[2]), "+l"(acc[3])
+            : "l"(x[0]), "l"(x[1]), "l"(x[2]), "l"(x[3]));
     }
 }
-template <int K>
-__device__ __forceinline__ void words_sub(unsigned long long (&acc)[3], const unsigned long long (&x)[3]) {
+template <int K, int NA, int NX>
+__device__ __forceinline__ void words_sub(unsigned long long (&acc)[NA], const unsigned long long (&x)[NX]) {
+    static_assert(K <= NA && K <= NX, "word count");
     if constexpr (K == 1) {
         acc[0] -= x[0];
     } else if constexpr (K == 2) {
@@ -220,7 +232,7 @@ __device__ __forceinline__ void limbs_mul_u32(unsigned (&p)[L], unsigned g) {
 
 // prod_i r_i modulo 2^W into x[0..W/64-1].
 template <int N, int W>
-__device__ __forceinline__ void row_product(const unsigned (&r)[N], unsigned long long (&x)[3]) {
+__device__ __forceinline__ void row_product(const unsigned (&r)[N], AccWords& x) {
     constexpr int kGroups = (N + 5) / 6;
     unsigned g[kGroups];
 #pragma unroll
@@ -247,7 +259,7 @@ __device__ __forceinline__ void row_product(const unsigned (&r)[N], unsigned lon
     }
 }
 template <int N, int W>
-__device__ __forceinline__ void row_product(const unsigned long long (&r)[N], unsigned long long (&x)[3]) {
+__device__ __forceinline__ void row_product(const unsigned long long (&r)[N], AccWords& x) {
     if constexpr (N == 1) {
         x[0] = r[0];
         if constexpr (W >= 128) x[1] = 0ull;
@@ -292,7 +304,7 @@ __device__ __forceinline__ void row_product(const unsigned long long (&r)[N], un
 // s_col: column j of A at s_col[j * NP .. j * NP + N - 1].
 template <int N, int NP, int W, typename E>
 __device__ __forceinline__ void ryser_int_range(const E* __restrict__ s_col, unsigned long long g0,
-                                                int log_len, unsigned long long (&acc)[3]) {
+                                                int log_len, AccWords& acc) {
     constexpr int K = W / 64;
     const unsigned long long gr0 = g0 ^ (g0 >> 1);
     E r[N];
@@ -309,7 +321,9 @@ __device__ __forceinline__ void ryser_int_range(const E* __restrict__ s_col, uns
     // log_len <= 9 and g0 is a multiple of 2^log_len: the walk flips only low bits
     unsigned grl = (unsigned)gr0;
     const unsigned len = 1u << log_len;
-    unsigned long long a[3] = {acc[0], acc[1], acc[2]};
+    unsigned long long a[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) a[k] = acc[k];
     for (unsigned st = 0; st < len; st++) {
         if (st > 0) {
             const int j = __ffs(st) - 1;                // the same column for the whole warp
@@ -324,14 +338,13 @@ __device__ __forceinline__ void ryser_int_range(const E* __restrict__ s_col, uns
             }
             neg ^= 1;
         }
-        unsigned long long x[3];
+        AccWords x;
         row_product<N, W>(r, x);
         if (neg) words_sub<K>(a, x);
         else words_add<K>(a, x);
     }
-    acc[0] = a[0];
-    acc[1] = a[1];
-    acc[2] = a[2];
+#pragma unroll
+    for (int k = 0; k < K; k++) acc[k] = a[k];
 }
 
 // ---------------------------------------------------------------------------
@@ -375,7 +388,7 @@ constexpr unsigned long long kRowBound1 = 127, kRowBound2 = 32767;   // integer 
 template <int N, int NP, int L, int G>
 __device__ __forceinline__ void glynn_range(const int* __restrict__ s_col2, const int* __restrict__ s_row,
                                             unsigned long long g0, int log_len,
-                                            unsigned long long (&acc)[3]) {
+                                            AccWords& acc) {
     constexpr int K = (L + 1) / 2;                 // 64-bit words of the accumulator
     constexpr int kGroups = (N + G - 1) / G;
     const unsigned long long gr0 = g0 ^ (g0 >> 1);
@@ -392,7 +405,9 @@ __device__ __forceinline__ void glynn_range(const int* __restrict__ s_col2, cons
     unsigned grl = (unsigned)gr0;                   // low word of the Gray code
     unsigned ncount = 0;                            // negative terms added as complements
     const unsigned len = 1u << log_len;
-    unsigned long long a[3] = {acc[0], acc[1], acc[2]};
+    unsigned long long a[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) a[k] = acc[k];
     for (unsigned st = 0; st < len; st++) {
         if (st > 0) {
             const int b = __ffs(st) - 1;            // the same flip for the whole warp
@@ -428,7 +443,7 @@ __device__ __forceinline__ void glynn_range(const int* __restrict__ s_col2, cons
             for (int q = 1; q < kGroups; q++) limbs_mul_u32<L>(p, (unsigned)abs(g[q]));
             // sgn ? ~|P| : |P| modulo 2^(64 K); the missing +1 of -|P| = ~|P| + 1 is counted
             const unsigned long long m = 0ull - (unsigned long long)sgn;
-            unsigned long long x[3] = {0ull, 0ull, 0ull};
+            unsigned long long x[K];
 #pragma unroll
             for (int k = 0; k < K; k++) {
                 const unsigned long long hi = (2 * k + 1 < L) ? ((unsigned long long)p[2 * k + 1] << 32) : 0ull;
@@ -438,14 +453,15 @@ __device__ __forceinline__ void glynn_range(const int* __restrict__ s_col2, cons
             ncount += sgn;
         }
     }
-    const unsigned long long c[3] = {(unsigned long long)ncount, 0ull, 0ull};
+    unsigned long long c[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) c[k] = k == 0 ? (unsigned long long)ncount : 0ull;
     words_add<K>(a, c);
-    acc[0] = a[0];
-    acc[1] = a[1];
-    acc[2] = a[2];
+#pragma unroll
+    for (int k = 0; k < K; k++) acc[k] = a[k];
 }
 
-// Bit-sliced variant for 12 <= n <= 32 (full warps, one 32-bit word per row set).
+// Bit-sliced variant for 12 <= n <= 40 (full warps, one word per row set).
 // Let c_i be the number of ones of row i among the columns with d_j = -1, so that
 // rho_i = R_i - 2 c_i.  A thread keeps the c_i of all rows as bit planes
 // (plane k holds bit k of every c_i): flipping column j adds or subtracts the
@@ -462,22 +478,26 @@ constexpr int count_planes() {
     return p;                     // bits of 0..N
 }
 
+__device__ __forceinline__ int popcnt(unsigned x) { return __popc(x); }
+__device__ __forceinline__ int popcnt(unsigned long long x) { return __popcll(x); }
+
 // The Glynn term of one code (d_j = -1 iff bit j - 1 of `code`), added to `a` as
 // described for glynn_range.  s_rm[i]: bit j - 1 set iff a_ij = 1 (j >= 1).
-template <int N, int L>
-__device__ __forceinline__ void glynn_term_from_code(unsigned code, const unsigned* __restrict__ s_rm,
+// M: an unsigned type wide enough for n rows (32 or 64 bits).
+template <int N, int L, typename M>
+__device__ __forceinline__ void glynn_term_from_code(M code, const M* __restrict__ s_rm,
                                                      const int* __restrict__ s_row,
-                                                     unsigned long long (&a)[3], unsigned& ncount) {
+                                                     unsigned long long (&a)[(L + 1) / 2], unsigned& ncount) {
     constexpr int K = (L + 1) / 2;
     constexpr int G = glynn_group<N, N>();
     constexpr int kGroups = (N + G - 1) / G;
-    unsigned sgn = (unsigned)__popc(code) & 1u;
+    unsigned sgn = (unsigned)popcnt(code) & 1u;
     int g[kGroups];
 #pragma unroll
     for (int q = 0; q < kGroups; q++) {
-        g[q] = s_row[q * G] - 2 * __popc(code & s_rm[q * G]);
+        g[q] = s_row[q * G] - 2 * popcnt(code & s_rm[q * G]);
 #pragma unroll
-        for (int i = q * G + 1; i < q * G + G && i < N; i++) g[q] *= s_row[i] - 2 * __popc(code & s_rm[i]);
+        for (int i = q * G + 1; i < q * G + G && i < N; i++) g[q] *= s_row[i] - 2 * popcnt(code & s_rm[i]);
         sgn ^= (unsigned)g[q] >> 31;
     }
     unsigned p[L];
@@ -487,7 +507,7 @@ __device__ __forceinline__ void glynn_term_from_code(unsigned code, const unsign
 #pragma unroll
     for (int q = 1; q < kGroups; q++) limbs_mul_u32<L>(p, (unsigned)abs(g[q]));
     const unsigned long long m = 0ull - (unsigned long long)sgn;
-    unsigned long long x[3] = {0ull, 0ull, 0ull};
+    unsigned long long x[K];
 #pragma unroll
     for (int k = 0; k < K; k++) {
         const unsigned long long hi = (2 * k + 1 < L) ? ((unsigned long long)p[2 * k + 1] << 32) : 0ull;
@@ -499,78 +519,82 @@ __device__ __forceinline__ void glynn_term_from_code(unsigned code, const unsign
 
 // One thread's range of 2^log_len codes from g0 (a multiple of 2^log_len);
 // called by every lane of full warps with the same log_len.  q: this warp's
-// 64-entry queue.  s_cm[j]: bit i set iff a_ij = 1.
-template <int N, int L>
-__device__ __forceinline__ void glynn_bits_range(const unsigned* __restrict__ s_cm, const unsigned* __restrict__ s_rm,
-                                                 const int* __restrict__ s_row, unsigned* q,
-                                                 unsigned g0, int log_len, unsigned long long (&acc)[3]) {
+// 64-entry queue.  s_cm[j]: bit i set iff a_ij = 1.  M: row-set words (32 bits
+// for n <= 32, else 64).
+template <int N, int L, typename M>
+__device__ __forceinline__ void glynn_bits_range(const M* __restrict__ s_cm, const M* __restrict__ s_rm,
+                                                 const int* __restrict__ s_row, M* q,
+                                                 M g0, int log_len, AccWords& acc) {
     constexpr int K = (L + 1) / 2;
     constexpr int NPL = count_planes<N>();
     const unsigned lane = threadIdx.x & 31u;
-    unsigned gr = g0 ^ (g0 >> 1);
+    M gr = g0 ^ (g0 >> 1);
     // target planes: rows of even R_i, h_i = R_i / 2
-    unsigned H[NPL], P[NPL];
-    unsigned even = 0u;
+    M H[NPL], P[NPL];
+    M even = 0;
 #pragma unroll
-    for (int k = 0; k < NPL; k++) { H[k] = 0u; P[k] = 0u; }
+    for (int k = 0; k < NPL; k++) { H[k] = 0; P[k] = 0; }
 #pragma unroll
     for (int i = 0; i < N; i++) {
         const int R = s_row[i];
-        const unsigned c = (unsigned)__popc(gr & s_rm[i]);
-        if ((R & 1) == 0) even |= 1u << i;
+        const unsigned c = (unsigned)popcnt(gr & s_rm[i]);
+        if ((R & 1) == 0) even |= (M)1 << i;
 #pragma unroll
         for (int k = 0; k < NPL; k++) {
-            H[k] |= (((unsigned)(R >> 1) >> k) & 1u) << i;
-            P[k] |= ((c >> k) & 1u) << i;
+            H[k] |= (M)(((unsigned)(R >> 1) >> k) & 1u) << i;
+            P[k] |= (M)((c >> k) & 1u) << i;
         }
     }
     unsigned qn = 0;                 // entries in the queue (the same in every lane)
     unsigned ncount = 0;
-    unsigned long long a[3] = {acc[0], acc[1], acc[2]};
+    unsigned long long a[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) a[k] = acc[k];
     const unsigned len = 1u << log_len;
     for (unsigned st = 0; st < len; st++) {
         if (st > 0) {
             const int b = __ffs(st) - 1;     // the same flip for the whole warp
-            gr ^= 1u << b;
-            const unsigned M = s_cm[b + 1];
-            if ((gr >> b) & 1u) {            // d_{b+1}: +1 -> -1, c_i += 1 on the rows of M
-                unsigned cy = M;
+            gr ^= (M)1 << b;
+            const M msk = s_cm[b + 1];
+            if ((gr >> b) & 1u) {            // d_{b+1}: +1 -> -1, c_i += 1 on the rows of msk
+                M cy = msk;
 #pragma unroll
-                for (int k = 0; k < NPL; k++) { const unsigned t = P[k] & cy; P[k] ^= cy; cy = t; }
+                for (int k = 0; k < NPL; k++) { const M t = P[k] & cy; P[k] ^= cy; cy = t; }
             } else {                         // -1 -> +1, c_i -= 1
-                unsigned bw = M;
+                M bw = msk;
 #pragma unroll
-                for (int k = 0; k < NPL; k++) { const unsigned t = ~P[k] & bw; P[k] ^= bw; bw = t; }
+                for (int k = 0; k < NPL; k++) { const M t = ~P[k] & bw; P[k] ^= bw; bw = t; }
             }
         }
-        unsigned diff = 0u;
+        M diff = 0;
 #pragma unroll
         for (int k = 0; k < NPL; k++) diff |= P[k] ^ H[k];
-        const bool live = (even & ~diff) == 0u;   // no rho_i is zero
+        const bool live = (even & ~diff) == 0;    // no rho_i is zero
         const unsigned ball = __ballot_sync(0xffffffffu, live);
         if (ball) {
             if (live) q[qn + __popc(ball & ((1u << lane) - 1u))] = gr;
             qn += (unsigned)__popc(ball);
             if (qn >= 32u) {
                 __syncwarp();
-                const unsigned code = q[lane];
-                const unsigned rest = lane < qn - 32u ? q[32u + lane] : 0u;
+                const M code = q[lane];
+                const M rest = lane < qn - 32u ? q[32u + lane] : (M)0;
                 __syncwarp();
                 if (lane < qn - 32u) q[lane] = rest;
                 qn -= 32u;
                 __syncwarp();
-                glynn_term_from_code<N, L>(code, s_rm, s_row, a, ncount);
+                glynn_term_from_code<N, L, M>(code, s_rm, s_row, a, ncount);
             }
         }
     }
     __syncwarp();
-    if (lane < qn) glynn_term_from_code<N, L>(q[lane], s_rm, s_row, a, ncount);
+    if (lane < qn) glynn_term_from_code<N, L, M>(q[lane], s_rm, s_row, a, ncount);
     __syncwarp();
-    const unsigned long long c[3] = {(unsigned long long)ncount, 0ull, 0ull};
+    unsigned long long c[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) c[k] = k == 0 ? (unsigned long long)ncount : 0ull;
     words_add<K>(a, c);
-    acc[0] = a[0];
-    acc[1] = a[1];
-    acc[2] = a[2];
+#pragma unroll
+    for (int k = 0; k < K; k++) acc[k] = a[k];
 }
 
 // Widest modulus an order-N matrix of the given kind can need: a 0/1 matrix
@@ -594,16 +618,17 @@ ryser_int_kernel(const long long* __restrict__ mats, const ItemDesc* __restrict_
                  IPartial* __restrict__ partials) {
     using E = typename std::conditional<ZO, unsigned, unsigned long long>::type;
     constexpr int NP = ZO ? ((N + 3) & ~3) : ((N + 1) & ~1);   // 16-byte columns
-    constexpr bool kEq4 = ZO ? N >= 35 : PATH != kPathGlynn;    // Eq. (4) codes needed
+    constexpr bool kEq4 = !ZO && PATH != kPathGlynn;            // Eq. (4) codes needed
     __shared__ __align__(16) E s_col[kEq4 ? N * NP : 1];        // s_col[j * NP + i] = a_ij
     __shared__ __align__(16) int s_col2[N * NP];                // Glynn: 2 a_ij
     __shared__ int s_row[NP];                                   // Glynn: sum_j a_ij
     __shared__ int s_cls;                                       // integers: row-sum class
     constexpr bool kBits = ZO && N >= 12 && N <= 32;            // bit-sliced Glynn walk
-    __shared__ unsigned s_cm[kBits ? N : 1];                    // bit i: a_ij = 1
-    __shared__ unsigned s_rm[kBits ? N : 1];                    // bit j - 1: a_ij = 1 (j >= 1)
-    __shared__ unsigned s_q[kBits ? kRyserThreads / 32 : 1][kBits ? 64 : 1];   // per-warp queues
-    __shared__ unsigned long long s_acc[3][kRyserThreads];
+    using M = unsigned;
+    __shared__ M s_cm[kBits ? N : 1];                           // bit i: a_ij = 1
+    __shared__ M s_rm[kBits ? N : 1];                           // bit j - 1: a_ij = 1 (j >= 1)
+    __shared__ M s_q[kBits ? kRyserThreads / 32 : 1][kBits ? 64 : 1];   // per-warp queues
+    __shared__ unsigned long long s_acc[kAccWords][kRyserThreads];
     __shared__ int s_width;
     constexpr int G = N;
     constexpr long long kParts = (G > kLogCodesPerPart) ? (1ll << (G - kLogCodesPerPart)) : 1ll;
@@ -615,6 +640,7 @@ ryser_int_kernel(const long long* __restrict__ mats, const ItemDesc* __restrict_
     constexpr int kLogThrG = kLogPartG >= 8 ? 8 : kLogPartG;
     constexpr int kLogLenG = kLogPartG - kLogThrG;
     constexpr int kL64 = (64 + N - 1 + 31) / 32, kL128 = (128 + N - 1 + 31) / 32;
+    constexpr int kL192 = (192 + N - 1 + 31) / 32;
     constexpr int kMaxW = max_width<N, ZO>();
     constexpr int kG01 = glynn_group<N, N>();                   // |rho_i| <= n
     constexpr int kG1 = glynn_group<kRowBound1, N>(), kG2 = glynn_group<kRowBound2, N>();
@@ -627,7 +653,7 @@ ryser_int_kernel(const long long* __restrict__ mats, const ItemDesc* __restrict_
         __syncthreads();
         if (threadIdx.x == 0) {
             s_width = widths[task / kParts];
-            s_cls = ZO ? 0 : widths[count + task / kParts];
+            s_cls = widths[count + task / kParts];
         }
         __syncthreads();
         const int w = s_width;
@@ -652,34 +678,37 @@ ryser_int_kernel(const long long* __restrict__ mats, const ItemDesc* __restrict_
         if constexpr (kBits) {
             if (threadIdx.x < N) {
                 const int t = threadIdx.x;
-                unsigned cm = 0u, rm = 0u;
-                for (int i = 0; i < N; i++) cm |= (a[i * N + t] != 0 ? 1u : 0u) << i;
-                for (int j = 1; j < N; j++) rm |= (a[t * N + j] != 0 ? 1u : 0u) << (j - 1);
+                M cm = 0, rm = 0;
+                for (int i = 0; i < N; i++) cm |= (M)(a[i * N + t] != 0 ? 1u : 0u) << i;
+                for (int j = 1; j < N; j++) rm |= (M)(a[t * N + j] != 0 ? 1u : 0u) << (j - 1);
                 s_cm[t] = cm;
                 s_rm[t] = rm;
             }
         }
         __syncthreads();
         int shift = 0;                  // Glynn: the sum is 2^(n-1) per(A)
-        unsigned long long acc[3] = {0ull, 0ull, 0ull};
+        AccWords acc = {0ull, 0ull, 0ull, 0ull};
         if constexpr (ZO) {
-            if (cw == 64 || cw == 128) {
+            if (cw > 0) {               // every width by Glynn's form
                 shift = N - 1;
                 if (threadIdx.x < (1 << kLogThrG)) {
                     const unsigned long long g0 = ((unsigned long long)part << kLogPartG) +
                                                   ((unsigned long long)threadIdx.x << kLogLenG);
                     if constexpr (kBits) {
                         // every thread of the CTA takes part (kLogThrG = 8): full warps
-                        unsigned* q = s_q[threadIdx.x >> 5];
-                        if (cw == 64) glynn_bits_range<N, kL64>(s_cm, s_rm, s_row, q, (unsigned)g0, kLogLenG, acc);
+                        M* q = s_q[threadIdx.x >> 5];
+                        if (cw == 64) glynn_bits_range<N, kL64, M>(s_cm, s_rm, s_row, q, (M)g0, kLogLenG, acc);
                         if constexpr (kMaxW >= 128) {
                             if (cw == 128)
-                                glynn_bits_range<N, kL128>(s_cm, s_rm, s_row, q, (unsigned)g0, kLogLenG, acc);
+                                glynn_bits_range<N, kL128, M>(s_cm, s_rm, s_row, q, (M)g0, kLogLenG, acc);
                         }
                     } else {
                         if (cw == 64) glynn_range<N, NP, kL64, kG01>(s_col2, s_row, g0, kLogLenG, acc);
                         if constexpr (kMaxW >= 128) {
                             if (cw == 128) glynn_range<N, NP, kL128, kG01>(s_col2, s_row, g0, kLogLenG, acc);
+                        }
+                        if constexpr (kMaxW >= 192) {
+                            if (cw == 192) glynn_range<N, NP, kL192, kG01>(s_col2, s_row, g0, kLogLenG, acc);
                         }
                     }
                 }
@@ -715,27 +744,27 @@ ryser_int_kernel(const long long* __restrict__ mats, const ItemDesc* __restrict_
                 }
             }
         }
-        s_acc[0][threadIdx.x] = acc[0];
-        s_acc[1][threadIdx.x] = acc[1];
-        s_acc[2][threadIdx.x] = acc[2];
+#pragma unroll
+        for (int k = 0; k < kAccWords; k++) s_acc[k][threadIdx.x] = acc[k];
         __syncthreads();
         for (int h = kRyserThreads / 2; h > 0; h >>= 1) {
             if (threadIdx.x < h) {
-                unsigned long long x[3] = {s_acc[0][threadIdx.x + h], s_acc[1][threadIdx.x + h],
-                                           s_acc[2][threadIdx.x + h]};
-                unsigned long long y[3] = {s_acc[0][threadIdx.x], s_acc[1][threadIdx.x], s_acc[2][threadIdx.x]};
-                words_add<3>(y, x);
-                s_acc[0][threadIdx.x] = y[0];
-                s_acc[1][threadIdx.x] = y[1];
-                s_acc[2][threadIdx.x] = y[2];
+                AccWords x, y;
+#pragma unroll
+                for (int k = 0; k < kAccWords; k++) {
+                    x[k] = s_acc[k][threadIdx.x + h];
+                    y[k] = s_acc[k][threadIdx.x];
+                }
+                words_add<kAccWords>(y, x);
+#pragma unroll
+                for (int k = 0; k < kAccWords; k++) s_acc[k][threadIdx.x] = y[k];
             }
             __syncthreads();
         }
         if (threadIdx.x == 0) {
             IPartial p;
-            p.w0 = s_acc[0][0];
-            p.w1 = s_acc[1][0];
-            p.w2 = s_acc[2][0];
+#pragma unroll
+            for (int k = 0; k < kAccWords; k++) p.w[k] = s_acc[k][0];
             p.meta = (unsigned long long)(unsigned)width_status(w) | ((unsigned long long)cw << 32) |
                      ((unsigned long long)shift << 48);
             partials[task] = p;
@@ -783,25 +812,27 @@ __global__ void ryser_finish_int(const ItemDesc* items, long long parts, int cou
                                  int* item_status) {
     const int it = blockIdx.x;
     if (it >= count) return;
-    __shared__ unsigned long long s[3][128];
-    unsigned long long acc[3] = {0ull, 0ull, 0ull};
+    __shared__ unsigned long long s[kAccWords][128];
+    AccWords acc = {0ull, 0ull, 0ull, 0ull};
     const long long b = (long long)it * parts, e = b + parts;
     for (long long p = b + threadIdx.x; p < e; p += blockDim.x) {
-        const unsigned long long x[3] = {partials[p].w0, partials[p].w1, partials[p].w2};
-        words_add<3>(acc, x);
+        const AccWords x = {partials[p].w[0], partials[p].w[1], partials[p].w[2], partials[p].w[3]};
+        words_add<kAccWords>(acc, x);
     }
-    s[0][threadIdx.x] = acc[0];
-    s[1][threadIdx.x] = acc[1];
-    s[2][threadIdx.x] = acc[2];
+#pragma unroll
+    for (int k = 0; k < kAccWords; k++) s[k][threadIdx.x] = acc[k];
     __syncthreads();
     for (int h = 64; h > 0; h >>= 1) {
         if (threadIdx.x < h) {
-            unsigned long long y[3] = {s[0][threadIdx.x], s[1][threadIdx.x], s[2][threadIdx.x]};
-            const unsigned long long x[3] = {s[0][threadIdx.x + h], s[1][threadIdx.x + h], s[2][threadIdx.x + h]};
-            words_add<3>(y, x);
-            s[0][threadIdx.x] = y[0];
-            s[1][threadIdx.x] = y[1];
-            s[2][threadIdx.x] = y[2];
+            AccWords x, y;
+#pragma unroll
+            for (int k = 0; k < kAccWords; k++) {
+                x[k] = s[k][threadIdx.x + h];
+                y[k] = s[k][threadIdx.x];
+            }
+            words_add<kAccWords>(y, x);
+#pragma unroll
+            for (int k = 0; k < kAccWords; k++) s[k][threadIdx.x] = y[k];
         }
         __syncthreads();
     }
@@ -812,9 +843,10 @@ __global__ void ryser_finish_int(const ItemDesc* items, long long parts, int cou
         const int sh = (int)((meta >> 48) & 0xffull);
         unsigned long long v0 = s[0][0], v1 = s[1][0], v2 = s[2][0];
         if (sh > 0) {       // exact division of Glynn's sum by 2^(n-1)
+            const unsigned long long v3 = s[3][0];
             v0 = (v0 >> sh) | (v1 << (64 - sh));
             v1 = (v1 >> sh) | (v2 << (64 - sh));
-            v2 >>= sh;
+            v2 = (v2 >> sh) | (v3 << (64 - sh));
         }
         const int o = items[it].out_index;
         unsigned long long* dst = out + (size_t)out_words * o;
@@ -838,6 +870,13 @@ __global__ void ryser_widths_kernel(const long long* mats, const ItemDesc* items
     const long long* a = mats + items[i].offset;
     const int w = decide_width_warp(a, n, zero_one != 0, allow192 != 0);
     const int lane = threadIdx.x & 31;
+    if (zero_one) {             // the class is used by general integers only
+        if (lane == 0) {
+            widths[i] = w;
+            widths[count + i] = 0;
+        }
+        return;
+    }
     unsigned long long rmax = 0ull;
     for (int r = lane; r < n; r += 32) {
         unsigned long long rs = 0ull;
@@ -910,8 +949,8 @@ using NTable = Table<PERM_NS>;
 
 
 // Launch Ryser for `count` matrices that all have order n (1 <= n <= 40);
-// `partials` holds count * ryser_parts(dtype, n) 32-byte slots and `widths`
-// 2 * count ints (integer types only).
+// `partials` holds count * ryser_parts(dtype, n) slots of ryser_partial_bytes(dtype)
+// and `widths` 2 * count ints (integer types only).
 cudaError_t ryser_launch_group(int dtype, int n, const void* mats, const ItemDesc* items, int count,
                                void* partials, int* widths, void* out, int out_words, bool allow192,
                                int* item_status, int grid, cudaStream_t st) {
@@ -940,6 +979,8 @@ cudaError_t ryser_launch_group(int dtype, int n, const void* mats, const ItemDes
 }
 
 long long ryser_parts(int dtype, int n) { return parts_for(dtype, n); }
+
+size_t ryser_partial_bytes(int dtype) { return dtype == PERM_C128 ? sizeof(CPartial) : sizeof(IPartial); }
 
 cudaError_t ryser_preload(int dtype, int n_max) {
     cudaFuncAttributes fa;
