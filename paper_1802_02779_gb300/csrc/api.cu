@@ -115,11 +115,16 @@ void release(T*& p) {
 perm_status cuda_status(cudaError_t e) { return e == cudaSuccess ? PERM_OK : PERM_ECUDA; }
 
 int sz_batch_limit(perm_plan_t p) {
-    // One CTA per matrix when the per-CTA chain workspace stays <= 80 MB.
+    // One CTA per matrix when the per-CTA chain workspace stays <= 80 MB.  For complex
+    // matrices at most n = 20: measured on GB300 (batches of 512-4096 matrices), the layer
+    // path, with every same-order matrix in each layer launch, is 3-11% faster at n = 21-22,
+    // where a batch leaves the one-CTA-per-matrix kernel a long last wave; the batched kernel
+    // is 4-8% faster up to n = 19.  Both give the same bits.
     int best = 0;
     for (int n = 1; n <= std::min(p->n_max, kMaxNSZ); n++) {
         if (sz_matrix_workspace_bytes(p->dtype, n, p->m_low) <= (size_t)80 << 20) best = n;
     }
+    if (p->dtype == PERM_C128) best = std::min(best, 20);
     return best;
 }
 
@@ -211,6 +216,12 @@ static perm_status plan_create_core(int n_max, perm_dtype dtype, const perm_opts
     const bool uses_sz = p->method == PERM_METHOD_SZ || (p->method == PERM_METHOD_AUTO && auto_uses_sz(dtype));
     if (uses_sz && n_max >= 1) {
         p->sz_batch_nmax = sz_batch_limit(p);
+        // experiment knob: largest order of the one-CTA-per-matrix kernel (the others take the
+        // layer path; both give the same bits)
+        if (const char* v = getenv("LIBPERM_SZ_BATCH_NMAX")) {
+            const int x = atoi(v);
+            if (x >= 0 && x < p->sz_batch_nmax) p->sz_batch_nmax = x;
+        }
         p->sz_ws_per_cta = sz_matrix_workspace_bytes(dtype, p->sz_batch_nmax, p->m_low);
         if (sz_init_tables() != cudaSuccess) { delete p; return PERM_ECUDA; }
         int per_sm = o.ctas_per_sm ? o.ctas_per_sm
