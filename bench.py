@@ -51,7 +51,7 @@ def parse():
                     help="single: one matrix of order --n with --method (for profiling)")
     ap.add_argument("--n", type=int, default=32)
     ap.add_argument("--method", default="sz", choices=["sz", "ryser"])
-    ap.add_argument("--dtype", default="c128", choices=["c128", "u01"])
+    ap.add_argument("--dtype", default="c128", choices=["c128", "u01", "i64"])
     ap.add_argument("--no-autotune", action="store_true",
                     help="use the default CTA size and chain width (profiling runs)")
     ap.add_argument("--int-method", default="auto", choices=["auto", "sz"],
@@ -669,7 +669,10 @@ def run_single(args):
         dev = torch.from_numpy(a.reshape(-1)).cuda()
         out = torch.empty(1, dtype=torch.complex128, device="cuda")
     else:
-        a = wl.bernoulli01(1, args.n, 0.5, wl.SEED_BASE + 4)[0]
+        if args.dtype == "u01":
+            a = wl.bernoulli01(1, args.n, 0.5, wl.SEED_BASE + 4)[0]
+        else:   # small integers 0..2
+            a = np.random.default_rng(wl.SEED_BASE + 4).integers(0, 3, (args.n, args.n)).astype(np.int64)
         dev = torch.from_numpy(a.reshape(-1)).cuda()
         out = torch.empty((1, 2), dtype=torch.int64, device="cuda")
     meth = lp.METHOD_SZ if args.method == "sz" else lp.METHOD_RYSER
