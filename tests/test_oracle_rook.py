@@ -67,3 +67,34 @@ def test_large_values_exceed_128_bits():
     for n, seed in ((35, 11), (38, 12), (40, 13)):
         v = per_complement(n, random_board(n, 12, seed))
         assert 2 ** 128 < v < math.factorial(n) < 2 ** 160
+
+
+@pytest.mark.parametrize("mistake", ["sign", "factorial", "attacking"])
+def test_planted_mistakes_are_caught(mistake):
+    """Plausible mistakes in the rook formula fail the pins above (derangements, brute force)."""
+    from oracle import rook
+
+    def wrong_rook_numbers(cells):
+        # counts every subset of cells, attacking or not
+        cs = sorted(set(cells))
+        return [math.comb(len(cs), k) for k in range(len(cs) + 1)]
+
+    def wrong(n, cells):
+        r = wrong_rook_numbers(cells) if mistake == "attacking" else rook.rook_numbers(cells)
+        total = 0
+        for k, rk in enumerate(r):
+            if k > n:
+                continue
+            sign = 1 if mistake == "sign" else (-1) ** k
+            fact = math.factorial(n - k - 1) if (mistake == "factorial" and n - k >= 1) else math.factorial(n - k)
+            total += sign * rk * fact
+        return total
+
+    caught = False
+    for n in (3, 5, 7):
+        if wrong(n, [(i, i) for i in range(n)]) != derangements(n):
+            caught = True
+    cells = random_board(6, 9, 3)
+    if wrong(6, cells) != oracle.per_brute(complement_matrix(6, cells)):
+        caught = True
+    assert caught, mistake
