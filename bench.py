@@ -117,10 +117,10 @@ class Clocks:
 
 
 # DRAM bytes (read + write) per n = 20 complex matrix of sz_batched_c128, from the ncu capture
-# summarised in profiles/sz_batched_c128_n20.md (304 matrices: 29.750804 GB + 7.624042 GB).
+# summarised in profiles/sz_batched_c128_n20.md (304 matrices: 29.754227 GB + 7.624871 GB).
 # Valid only for the kernel source it was measured on; otherwise the bench reports null.
-TRAFFIC_C128_PER_MATRIX = (29.750804e9 + 7.624042e9) / 304
-TRAFFIC_SOURCE_SHA256 = "17218d88051d3fc3f36347bb314cab34644d32f4458a3342f0998d6725150261"
+TRAFFIC_C128_PER_MATRIX = (29.754227e9 + 7.624871e9) / 304
+TRAFFIC_SOURCE_SHA256 = "b8ab79e02bc096d0744d08e057785e206a6c695a7ceb85b83844dcf1e8fe1413"
 
 
 def traffic_per_launch(count: int):

@@ -13,23 +13,24 @@
 // (The paper expands the last row first; read from the bottom up that is this
 // recurrence with level k built from row k-1.)
 //
-// GPU organisation ("chains").  The columns are split into m low columns
-// 0..m-1 and t = n-m high columns m..n-1.  Every set S is a pair (H, L) of a
-// high part and a low part.  A chain is the 2^m entries (H, L) of one high
-// subset H and all low subsets L.  The recurrence splits into
-//     low terms   j in L:  T[(H, L \ j)]  -- the same chain, |L| one smaller
-//     high terms  h in H:  T[(H \ h, L)]  -- another chain, same L
-// so one CTA computes one chain in shared memory sub-level by sub-level
-// (|L| = 0..m), gathering low parents from shared memory and streaming high
-// parents, coalesced, from the predecessor chains in global memory.  Chains
-// are processed in layers of |H| = 0..t; layer s needs only layer s-1.
+// GPU organisation ("chains").  The columns are split into t = n-m outer
+// columns 0..t-1 and m chain columns t..n-1.  Every set S is a pair (H, L) of
+// an outer part and a chain part.  A chain is the 2^m entries (H, L) of one
+// outer subset H and all chain subsets L.  The recurrence splits into
+//     outer terms  h in H:  T[(H \ h, L)]  -- another chain, same L
+//     chain terms  j in L:  T[(H, L \ j)]  -- the same chain, |L| one smaller
+// so one CTA computes one chain in shared memory: first every entry's outer
+// terms, streamed (coalesced) from the predecessor chains in global memory,
+// then sub-level by sub-level (|L| = 0..m) its chain terms, gathered from
+// shared memory.  Chains are processed in layers of |H| = 0..t; layer s needs
+// only layer s-1.
 //
 // Two layouts of a chain:
-//   shared memory  indexed by the bit mask of L (2^m slots), so the low parent
-//                  of (H, L) for column j is simply slot L ^ (1 << j);
+//   shared memory  indexed by the bit mask of L (2^m slots), so the chain
+//                  parent of (H, L) for chain column j is slot L ^ (1 << j);
 //   global memory  indexed by (|L|, colex rank of L): the entries of one
 //                  sub-level are contiguous, and the predecessor chains use the
-//                  same order, so high-parent reads are coalesced.
+//                  same order, so outer-parent reads are coalesced.
 // A table (g_masks) lists the masks in the global order.
 //
 // Complex entries use the three-multiplication form of the complex product
@@ -46,9 +47,10 @@
 // Integer entries are evaluated modulo 2^64 or 2^128 (exact under the bound
 // chosen by decide_width); zero coefficients skip their term.
 //
-// Summation order for every entry: low columns ascending, then high columns
-// ascending, i.e. all columns ascending.  The order depends only on (n, m),
-// never on the batch, the grid or the CTA.
+// Summation order for every entry: outer columns ascending, then chain
+// columns ascending, i.e. all columns ascending.  The order therefore depends
+// on none of m, the batch, the grid or the CTA: every kernel here gives every
+// matrix the same bits.
 #include "perm_internal.cuh"
 
 #include <algorithm>
