@@ -226,10 +226,11 @@ perm_status perm_patterns_multiset(const void *mats, int count, int rows, int co
                                    void *stream);
 
 /* Store-zechin permanent of ONE matrix without allocating any device memory.
-   The paper has no counterpart to this entry point; it exists for callers that
-   cannot call cudaMalloc: code running inside a framework whose pool owns all
-   device memory, loops that cannot afford the device-wide synchronisation an
-   allocation may cause, and threads in the middle of capturing a CUDA graph.
+   The paper has no counterpart to this entry point.  It exists for callers
+   that cannot call cudaMalloc: code inside a framework whose memory pool owns
+   every byte of device memory (an allocation behind the pool's back can fail or
+   starve it), and loops that cannot afford the device-wide synchronisation an
+   allocation may cause.
      mat          device pointer, n*n row-major elements of `dtype`
      out          device pointer: double2 (PERM_C128) or two uint64 (integers)
      item_status  device int or NULL (PERM_OK, PERM_EOVERFLOW, PERM_EINVAL)
@@ -238,16 +239,54 @@ perm_status perm_patterns_multiset(const void *mats, int count, int rows, int co
    exits.  That bounds n: at most 22 for PERM_C128 and 23 for the integer types;
    larger n (and n < 0, a bad dtype or a NULL pointer) return PERM_EINVAL and
    launch nothing.  n = 0 gives 1.
-   The first call on a device does a one-time set-up (it looks up the scratch
-   address and uploads a 16 KB index table with cudaMemcpyToSymbol), so make
+   The first call on a device does a one-time set-up with that device current
+   (it looks up the scratch address with cudaGetSymbolAddress and, unless a plan
+   already did, uploads a 16 KB index table with cudaMemcpyToSymbol), so make
    that first call before any stream capture.  The work is asynchronous on
    `stream`.  Every call shares the one scratch array, which keeps the last
    call's contents (nothing in it has to start at zero: every table entry is
    written before it is read); calls whose work overlaps on the GPU, from
    different streams or threads, race on it and must be serialised by the
-   caller.  Results are identical to perm_batch with PERM_METHOD_SZ. */
+   caller.  Results are bit-identical to perm_batch with PERM_METHOD_SZ. */
 perm_status perm_sz_noalloc(const void *mat, int n, perm_dtype dtype, void *out, int *item_status,
                             void *stream);
+
+/* ONE large matrix by Ryser's formula split over several GPUs (Section 3.3,
+   Eq. (4); for complex and 0/1 input Glynn's half-size form).  The codes of an
+   order-n matrix are cut into a fixed number of pieces (a function of n and
+   dtype only), the pieces perm_batch itself uses.  Each GPU (rank) computes the
+   partial sums of a contiguous range of pieces; the ranks' partial sums are
+   gathered in piece order (any transport: an all-gather, host copies), and one
+   finishing call sums all of them in perm_batch's fixed order.  The result is
+   therefore bit-identical to perm_batch with PERM_METHOD_RYSER, whatever the
+   number of ranks.
+     perm_ryser_pieces   host only (no GPU call): the number of pieces of an
+                         order-n matrix and the bytes of one piece's partial sum
+                         (32 for PERM_C128: two double-doubles; 40 for integers:
+                         a 256-bit modular sum and a word of width/status).
+                         PERM_EINVAL for n outside [1, 40] or a bad dtype.
+     perm_ryser_split    host only: rank's share [*begin, *end) of `pieces`
+                         pieces among `world` ranks (contiguous, balanced: sizes
+                         differ by at most one).  PERM_EINVAL for pieces < 1,
+                         world < 1 or rank outside [0, world).
+     perm_ryser_partials partial sums of pieces [begin, end) of the matrix `mat`
+                         (device, n*n elements of the plan's dtype) into
+                         `partials` (device, (end - begin) * piece bytes), async
+                         on `stream`.  The plan supplies dtype and width (its
+                         PERM_FLAG_WIDE) and 1 <= n <= its n_max, else
+                         PERM_EINVAL; begin == end launches nothing.
+     perm_ryser_finish   sums `partials` (device, ALL pieces of the matrix in
+                         piece order) and writes the permanent to `out` (device,
+                         as perm_batch writes one result) and `item_status`
+                         (device int or NULL), async on `stream`.
+   The calls of one plan must be ordered on the GPU (one stream), as for
+   perm_batch.  The caller owns every buffer. */
+perm_status perm_ryser_pieces(int n, perm_dtype dtype, long long *pieces, size_t *piece_bytes);
+perm_status perm_ryser_split(long long pieces, int rank, int world, long long *begin, long long *end);
+perm_status perm_ryser_partials(perm_plan_t plan, const void *mat, int n, long long begin, long long end,
+                                void *partials, void *stream);
+perm_status perm_ryser_finish(perm_plan_t plan, int n, const void *partials, void *out, int *item_status,
+                              void *stream);
 
 /* Short text for a status code (static storage). */
 const char *perm_strerror(perm_status status);

@@ -588,6 +588,73 @@ perm_status perm_batch_host(perm_plan_t p, const void* mats, const int* sizes, i
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
+// One large matrix split over several GPUs by Ryser's code range (Section 3.3,
+// Eq. 4 / Glynn's form).  The codes of an order-n matrix are cut into the
+// same pieces perm_batch uses; a rank computes the partial sums of a
+// contiguous range of pieces, the ranks' partial sums are gathered in piece
+// order, and one finishing call sums all of them in the fixed order
+// perm_batch uses.  So the result is the same bits for every number of ranks.
+// ---------------------------------------------------------------------------
+namespace {
+
+// Upload one descriptor {offset 0, order n, slot 0} through the plan's staging.
+perm_status stage_one(perm_plan_t p, int n, cudaStream_t st) {
+    const ItemDesc d{0, n, 0};
+    cudaError_t e = cudaEventSynchronize(p->stage_free);
+    if (e != cudaSuccess) return PERM_ECUDA;
+    std::memcpy(p->h_stage, &d, sizeof(d));
+    e = cudaMemcpyAsync(p->d_stage, p->h_stage, sizeof(d), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaEventRecord(p->stage_free, st);
+    return cuda_status(e);
+}
+
+}  // namespace
+
+extern "C" {
+
+perm_status perm_ryser_pieces(int n, perm_dtype dtype, long long* pieces, size_t* piece_bytes) {
+    if (!valid_dtype(dtype) || n < 1 || n > kMaxN || !pieces) return PERM_EINVAL;
+    *pieces = ryser_parts(dtype, n);
+    if (piece_bytes) *piece_bytes = ryser_partial_bytes(dtype);
+    return PERM_OK;
+}
+
+perm_status perm_ryser_split(long long pieces, int rank, int world, long long* begin, long long* end) {
+    if (pieces < 1 || world < 1 || rank < 0 || rank >= world || !begin || !end) return PERM_EINVAL;
+    // balanced contiguous ranges: rank r takes [floor(P r / W), floor(P (r+1) / W)); computed
+    // without overflow for P < 2^40 and W < 2^20
+    *begin = (long long)((unsigned long long)pieces * (unsigned long long)rank / (unsigned long long)world);
+    *end = (long long)((unsigned long long)pieces * (unsigned long long)(rank + 1) / (unsigned long long)world);
+    return PERM_OK;
+}
+
+perm_status perm_ryser_partials(perm_plan_t p, const void* mat, int n, long long begin, long long end,
+                                void* partials, void* stream) {
+    if (!p || !mat || !partials || n < 1 || n > p->n_max) return PERM_EINVAL;
+    if (begin < 0 || end < begin || end > ryser_parts(p->dtype, n)) return PERM_EINVAL;
+    if (begin == end) return PERM_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    perm_status ps = stage_one(p, n, st);
+    if (ps != PERM_OK) return ps;
+    const cudaError_t e = ryser_launch_pieces(p->dtype, n, mat, reinterpret_cast<const ItemDesc*>(p->d_stage),
+                                              begin, end, partials, p->d_widths, p->out_words == 4, 1 << 30, st);
+    return e == cudaErrorInvalidValue ? PERM_EINVAL : cuda_status(e);
+}
+
+perm_status perm_ryser_finish(perm_plan_t p, int n, const void* partials, void* out, int* item_status,
+                              void* stream) {
+    if (!p || !partials || !out || n < 1 || n > p->n_max) return PERM_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    perm_status ps = stage_one(p, n, st);
+    if (ps != PERM_OK) return ps;
+    const cudaError_t e = ryser_finish_one(p->dtype, n, reinterpret_cast<const ItemDesc*>(p->d_stage), partials,
+                                           out, p->out_words, item_status, st);
+    return cuda_status(e);
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
 // Autotuner (PERM_FLAG_AUTOTUNE).  Chooses the CTA size and the chain width of
 // the batched Store-zechin kernel by timing every candidate on a synthetic
 // batch of the plan's typical order; every candidate computes bit-identical

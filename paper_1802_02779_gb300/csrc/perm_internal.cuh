@@ -248,6 +248,17 @@ cudaError_t ryser_launch_group(int dtype, int n, const void* mats, const ItemDes
                                void* partials, int* widths, void* out, int out_words, bool allow192,
                                int* item_status, int grid, cudaStream_t st);
 
+// One matrix split into several launches (or GPUs): pieces [begin, end) of its
+// ryser_parts(dtype, n) pieces, partial sums to partials[0 .. end - begin);
+// then the finishing kernel over all of its pieces' partial sums (in piece
+// order), which gives the bits ryser_launch_group gives.  `item`: one device
+// descriptor; widths: 2 ints of scratch (integer types).
+cudaError_t ryser_launch_pieces(int dtype, int n, const void* mats, const ItemDesc* item, long long begin,
+                                long long end, void* partials, int* widths, bool allow192, int grid,
+                                cudaStream_t st);
+cudaError_t ryser_finish_one(int dtype, int n, const ItemDesc* item, const void* partials, void* out,
+                             int out_words, int* item_status, cudaStream_t st);
+
 // Load now every kernel a plan of this element type may launch (Ryser: orders
 // 1..n_max).  The runtime otherwise loads a kernel at its first launch, and
 // that load can wait for all work running on the device -- which would stall a

@@ -62,7 +62,8 @@ struct IPartial { unsigned long long w[4], meta; };
 template <int N>
 __global__ void __launch_bounds__(kRyserThreads)
 ryser_c128_kernel(const double2* __restrict__ mats, const ItemDesc* __restrict__ items,
-                  long long total_parts, CPartial* __restrict__ partials) {
+                  long long total_parts, long long part0, long long item_parts,
+                  CPartial* __restrict__ partials) {
     __shared__ double2 s_col[N > 0 ? N : 1][N > 0 ? N : 1];   // s_col[j][i] = 2 * a_ij
     __shared__ double2 s_row0[N > 0 ? N : 1];                  // full row sums sum_j a_ij (d = +1)
     __shared__ dd2 s_re[kRyserThreads], s_im[kRyserThreads];
@@ -73,9 +74,11 @@ ryser_c128_kernel(const double2* __restrict__ mats, const ItemDesc* __restrict__
     constexpr int kLogLen = kLogPart - kLogThr;                 // codes per thread = 2^kLogLen
 
     for (long long task = blockIdx.x; task < total_parts; task += gridDim.x) {
-        // every matrix of one launch has order N, hence kParts pieces
-        const ItemDesc d = items[task / kParts];
-        const long long part = task % kParts;
+        // every matrix of one launch has order N, hence kParts pieces; a launch takes
+        // pieces part0 .. part0 + item_parts - 1 of each (all of them unless a caller
+        // splits one matrix's pieces over several launches or GPUs)
+        const ItemDesc d = items[task / item_parts];
+        const long long part = part0 + task % item_parts;
         const double2* a = mats + d.offset;
         __syncthreads();
         for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
@@ -614,8 +617,8 @@ enum : int { kPathAll = 0, kPathGlynn = 1, kPathEq4 = 2 };
 template <int N, bool ZO, int PATH>
 __global__ void __launch_bounds__(kRyserThreads, (ZO || PATH == kPathGlynn) ? 3 : 2)
 ryser_int_kernel(const long long* __restrict__ mats, const ItemDesc* __restrict__ items,
-                 long long total_parts, const int* __restrict__ widths, int allow192,
-                 IPartial* __restrict__ partials) {
+                 long long total_parts, long long part0, long long item_parts,
+                 const int* __restrict__ widths, int allow192, IPartial* __restrict__ partials) {
     using E = typename std::conditional<ZO, unsigned, unsigned long long>::type;
     constexpr int NP = ZO ? ((N + 3) & ~3) : ((N + 1) & ~1);   // 16-byte columns
     constexpr bool kEq4 = !ZO && PATH != kPathGlynn;            // Eq. (4) codes needed
@@ -644,16 +647,16 @@ ryser_int_kernel(const long long* __restrict__ mats, const ItemDesc* __restrict_
     constexpr int kMaxW = max_width<N, ZO>();
     constexpr int kG01 = glynn_group<N, N>();                   // |rho_i| <= n
     constexpr int kG1 = glynn_group<kRowBound1, N>(), kG2 = glynn_group<kRowBound2, N>();
-    const long long count = total_parts / kParts;               // widths[count + i]: row-sum class
+    const long long count = total_parts / item_parts;           // widths[count + i]: row-sum class
 
     for (long long task = blockIdx.x; task < total_parts; task += gridDim.x) {
-        const ItemDesc d = items[task / kParts];
-        const long long part = task % kParts;
+        const ItemDesc d = items[task / item_parts];
+        const long long part = part0 + task % item_parts;           // as in ryser_c128_kernel
         const long long* a = mats + d.offset;
         __syncthreads();
         if (threadIdx.x == 0) {
-            s_width = widths[task / kParts];
-            s_cls = widths[count + task / kParts];
+            s_width = widths[task / item_parts];
+            s_cls = widths[count + task / item_parts];
         }
         __syncthreads();
         const int w = s_width;
@@ -896,25 +899,30 @@ __global__ void ryser_widths_kernel(const long long* mats, const ItemDesc* items
 
 template <int N>
 cudaError_t launch_n(int dtype, const void* mats, const ItemDesc* items, long long total_parts,
+                     long long part0, long long item_parts,
                      const int* widths, int allow192, void* partials, int grid, cudaStream_t st) {
     const int g = (int)std::min<long long>(total_parts, (long long)grid);
     if (dtype == PERM_C128) {
-        ryser_c128_kernel<N><<<g, kRyserThreads, 0, st>>>((const double2*)mats, items, total_parts,
+        ryser_c128_kernel<N><<<g, kRyserThreads, 0, st>>>((const double2*)mats, items, total_parts, part0,
+                                                          item_parts,
                                                           (CPartial*)partials);
     } else if (dtype == PERM_U01) {
         ryser_int_kernel<N, true, kPathAll><<<g, kRyserThreads, 0, st>>>(
-            (const long long*)mats, items, total_parts, widths, allow192, (IPartial*)partials);
+            (const long long*)mats, items, total_parts, part0, item_parts, widths, allow192,
+            (IPartial*)partials);
     } else {
         ryser_int_kernel<N, false, kPathGlynn><<<g, kRyserThreads, 0, st>>>(
-            (const long long*)mats, items, total_parts, widths, allow192, (IPartial*)partials);
+            (const long long*)mats, items, total_parts, part0, item_parts, widths, allow192,
+            (IPartial*)partials);
         ryser_int_kernel<N, false, kPathEq4><<<g, kRyserThreads, 0, st>>>(
-            (const long long*)mats, items, total_parts, widths, allow192, (IPartial*)partials);
+            (const long long*)mats, items, total_parts, part0, item_parts, widths, allow192,
+            (IPartial*)partials);
     }
     return cudaGetLastError();
 }
 
-typedef cudaError_t (*launch_fn)(int, const void*, const ItemDesc*, long long, const int*, int, void*,
-                                 int, cudaStream_t);
+typedef cudaError_t (*launch_fn)(int, const void*, const ItemDesc*, long long, long long, long long,
+                                 const int*, int, void*, int, cudaStream_t);
 
 // Load the kernels of order N for `dtype` now (cudaFuncGetAttributes makes the
 // runtime load a function): a lazy load at the first launch can wait for every
@@ -966,7 +974,7 @@ cudaError_t ryser_launch_group(int dtype, int n, const void* mats, const ItemDes
         cudaError_t e0 = cudaGetLastError();
         if (e0 != cudaSuccess) return e0;
     }
-    cudaError_t e = NTable::fns[n - 1](dtype, mats, items, (long long)count * parts, widths,
+    cudaError_t e = NTable::fns[n - 1](dtype, mats, items, (long long)count * parts, 0ll, parts, widths,
                                        allow192 ? 1 : 0, partials, grid, st);
     if (e != cudaSuccess) return e;
     if (dtype == PERM_C128)
@@ -975,6 +983,39 @@ cudaError_t ryser_launch_group(int dtype, int n, const void* mats, const ItemDes
     else
         ryser_finish_int<<<count, 128, 0, st>>>(items, parts, count, (const IPartial*)partials,
                                                 (unsigned long long*)out, out_words, item_status);
+    return cudaGetLastError();
+}
+
+// Pieces [begin, end) of one matrix's codes (item: one device descriptor), their
+// partial sums written to partials[0 .. end - begin).  The pieces are the ones
+// ryser_launch_group cuts, so the sums are the same bits.
+cudaError_t ryser_launch_pieces(int dtype, int n, const void* mats, const ItemDesc* item, long long begin,
+                                long long end, void* partials, int* widths, bool allow192, int grid,
+                                cudaStream_t st) {
+    if (n < 1 || n > kMaxN || begin < 0 || end > parts_for(dtype, n) || begin > end)
+        return cudaErrorInvalidValue;
+    if (begin == end) return cudaSuccess;
+    if (dtype != PERM_C128) {
+        ryser_widths_kernel<<<1, 128, 0, st>>>((const long long*)mats, item, 1, n, dtype == PERM_U01,
+                                               allow192 ? 1 : 0, widths);
+        const cudaError_t e0 = cudaGetLastError();
+        if (e0 != cudaSuccess) return e0;
+    }
+    return NTable::fns[n - 1](dtype, mats, item, end - begin, begin, end - begin, widths, allow192 ? 1 : 0,
+                              partials, grid, st);
+}
+
+// The finishing kernel of one matrix over all of its pieces' partial sums.
+cudaError_t ryser_finish_one(int dtype, int n, const ItemDesc* item, const void* partials, void* out,
+                             int out_words, int* item_status, cudaStream_t st) {
+    if (n < 1 || n > kMaxN) return cudaErrorInvalidValue;
+    const long long parts = parts_for(dtype, n);
+    if (dtype == PERM_C128)
+        ryser_finish_c128<<<1, 32, 0, st>>>(item, parts, 1, (const CPartial*)partials, (double2*)out,
+                                            item_status);
+    else
+        ryser_finish_int<<<1, 128, 0, st>>>(item, parts, 1, (const IPartial*)partials,
+                                            (unsigned long long*)out, out_words, item_status);
     return cudaGetLastError();
 }
 

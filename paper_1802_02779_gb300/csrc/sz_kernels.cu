@@ -738,8 +738,29 @@ cudaError_t set_smem(const void* fn, int bytes) {
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
+namespace {
+
+// The mask lists of every chain width m = 1..kMaxLow, ordered by (popcount,
+// value), as g_masks holds them.  Filled once into a static host array, so
+// uploading it allocates nothing.
+unsigned short g_masks_host[kMaskTableLen];
+std::once_flag g_masks_host_once;
+
+const unsigned short* mask_table_host() {
+    std::call_once(g_masks_host_once, [] {
+        int k = 0;
+        for (int m = 1; m <= kMaxLow; m++)
+            for (int l = 0; l <= m; l++)
+                for (unsigned x = 0; x < (1u << m); x++)
+                    if (__builtin_popcount(x) == l) g_masks_host[k++] = (unsigned short)x;
+    });
+    return g_masks_host;
+}
+
+}  // namespace
+
 cudaError_t sz_init_tables() {
-    // once per device: the mask lists, ordered by (popcount, value), for m = 1..kMaxLow
+    // once per device, with that device current
     static std::mutex mu;
     static std::vector<int> done;
     int dev = 0;
@@ -747,13 +768,7 @@ cudaError_t sz_init_tables() {
     if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> g(mu);
     if (std::find(done.begin(), done.end(), dev) != done.end()) return cudaSuccess;
-    std::vector<unsigned short> tab;
-    tab.reserve(kMaskTableLen);
-    for (int m = 1; m <= kMaxLow; m++)
-        for (int l = 0; l <= m; l++)
-            for (unsigned x = 0; x < (1u << m); x++)
-                if (__builtin_popcount(x) == l) tab.push_back((unsigned short)x);
-    e = cudaMemcpyToSymbol(g_masks, tab.data(), tab.size() * sizeof(unsigned short));
+    e = cudaMemcpyToSymbol(g_masks, mask_table_host(), sizeof(g_masks_host));
     if (e == cudaSuccess) done.push_back(dev);
     return e;
 }
@@ -928,10 +943,9 @@ cudaError_t launch_trivial(int dtype, const ItemDesc* items, int count, void* ou
 // ---------------------------------------------------------------------------
 // Allocation-free entry point (perm_sz_noalloc).
 //
-// Some callers cannot call cudaMalloc: a framework that owns every byte of
-// device memory through its own pool, code that must not take the implicit
-// device synchronisation an allocation can cause, or a thread that is in the
-// middle of capturing a CUDA graph.  For them this entry point runs the
+// Some callers cannot call cudaMalloc: a framework whose memory pool owns every
+// byte of device memory, or a loop that must not take the implicit device-wide
+// synchronisation an allocation can cause.  For them this entry point runs the
 // single-matrix Store-zechin path with its chain tables in a fixed scratch
 // array that lives in the library's device image instead of a plan.
 // ---------------------------------------------------------------------------
@@ -948,7 +962,6 @@ static __device__ __align__(256) unsigned long long g_noalloc_scratch[kNoAllocSc
 constexpr int kNoAllocMaxDevices = 64;
 std::mutex g_noalloc_mu;
 void* g_noalloc_ptr[kNoAllocMaxDevices] = {nullptr};
-unsigned short g_noalloc_hosttab[kMaskTableLen];
 
 __global__ void noalloc_write_one(int dtype, void* out, int* item_status) {
     if (dtype == PERM_C128) {
@@ -960,20 +973,16 @@ __global__ void noalloc_write_one(int dtype, void* out, int* item_status) {
     if (item_status) item_status[0] = PERM_OK;
 }
 
-// Once per device, with that device current: the scratch address and the
-// mask table (filled from a static host array, so nothing is allocated).
+// Once per device, with that device current: the scratch address, and the
+// mask table every chain kernel reads (sz_init_tables, the same upload the
+// plans use; it copies from a static host array and allocates nothing).
 cudaError_t noalloc_setup(int dev, void** scratch) {
     std::lock_guard<std::mutex> g(g_noalloc_mu);
     if (g_noalloc_ptr[dev]) { *scratch = g_noalloc_ptr[dev]; return cudaSuccess; }
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
-    int k = 0;
-    for (int m = 1; m <= kMaxLow; m++)
-        for (int l = 0; l <= m; l++)
-            for (unsigned x = 0; x < (1u << m); x++)
-                if (__builtin_popcount(x) == l) g_noalloc_hosttab[k++] = (unsigned short)x;
-    e = cudaMemcpyToSymbol(g_masks, g_noalloc_hosttab, sizeof(g_noalloc_hosttab));
+    e = sz_init_tables();
     if (e != cudaSuccess) return e;
     g_noalloc_ptr[dev] = p;
     *scratch = p;

@@ -65,6 +65,12 @@ _SIGS = {
     "perm_sz_noalloc": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP, _VP, _VP]),
     "perm_patterns": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _VP]),
     "perm_patterns_multiset": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _VP]),
+    "perm_ryser_pieces": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
+                                         ctypes.POINTER(ctypes.c_size_t)]),
+    "perm_ryser_split": (ctypes.c_int, [ctypes.c_longlong, ctypes.c_int, ctypes.c_int,
+                                        ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
+    "perm_ryser_partials": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_longlong, ctypes.c_longlong, _VP, _VP]),
+    "perm_ryser_finish": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP, _VP]),
 }
 
 _lib = None
@@ -178,6 +184,37 @@ class Plan:
                                     _VP(item_status.ctypes.data if item_status is not None else 0),
                                     _VP(_stream_ptr(stream) if stream is not None else 0))
         _check(rc, "perm_batch_host")
+
+
+    # -- one matrix split by Ryser code range (device buffers) --------------------------
+    def ryser_partials(self, mat, n: int, begin: int, end: int, partials, stream=None):
+        """Partial sums of pieces [begin, end) of one order-n device matrix into `partials`."""
+        rc = load().perm_ryser_partials(self._h, _VP(mat.data_ptr()), int(n), int(begin), int(end),
+                                        _VP(partials.data_ptr()), _VP(_stream_ptr(stream)))
+        _check(rc, "perm_ryser_partials")
+
+    def ryser_finish(self, n: int, partials, out, item_status=None, stream=None):
+        """The permanent from ALL pieces' partial sums (device, in piece order)."""
+        rc = load().perm_ryser_finish(self._h, int(n), _VP(partials.data_ptr()), _VP(out.data_ptr()),
+                                      _VP(item_status.data_ptr() if item_status is not None else 0),
+                                      _VP(_stream_ptr(stream)))
+        _check(rc, "perm_ryser_finish")
+
+
+def ryser_pieces(n: int, dtype: str):
+    """(pieces, bytes per piece) of Ryser's code range for one order-n matrix (host only)."""
+    pieces, nbytes = ctypes.c_longlong(), ctypes.c_size_t()
+    _check(load().perm_ryser_pieces(int(n), DTYPES[dtype], ctypes.byref(pieces), ctypes.byref(nbytes)),
+           "perm_ryser_pieces")
+    return int(pieces.value), int(nbytes.value)
+
+
+def ryser_split(pieces: int, rank: int, world: int):
+    """Rank's contiguous share [begin, end) of `pieces` pieces among `world` ranks (host only)."""
+    b, e = ctypes.c_longlong(), ctypes.c_longlong()
+    _check(load().perm_ryser_split(int(pieces), int(rank), int(world), ctypes.byref(b), ctypes.byref(e)),
+           "perm_ryser_split")
+    return int(b.value), int(e.value)
 
 
 def colex_subsets(cols: int, rows: int):
