@@ -409,6 +409,7 @@ def measure_extras(lp, torch, cm, im, stream, c_kernel_ms, count):
     out["wide"] = measure_wide(lp, torch, stream)
     out["five_boson"] = measure_five_boson(lp, torch, stream)
     out["uneven"] = measure_uneven(lp, torch, stream)
+    out["serving_n20"] = measure_serving_n20(lp)
     out["serving"] = measure_serving(lp)
     return out
 
@@ -561,57 +562,134 @@ def measure_uneven(lp, torch, stream, count=1000):
     return res
 
 
-def measure_serving(lp, arrival_window_s=60.0, drain_s=120.0):
-    """Serving loop under Poisson arrivals: n uniform in 10..36, 70% complex
-    Haar submatrices, 30% 0/1.  The arrival rate is 0.8 x the capacity measured
-    by serving one request of every order 10..36 (complex, the costlier kind)
-    back to back.  Latency = completion seen by perm_poll minus the scheduled
-    arrival."""
+def drive_server(srv, reqs, arrivals, limit_s, fifo=False):
+    """Submit every request at its scheduled arrival (seconds after the start) and
+    poll for completions.  fifo: poll in submission order and stop at the first
+    request still pending (requests of one lane complete in order).  Returns the
+    latencies (completion seen by perm_poll minus scheduled arrival), the orders
+    of the completed requests and the time of the last completion."""
+    pending = []
+    lat, lat_n = [], []
+    start = time.perf_counter()
+    last = 0.0
+    i = 0
+    while i < len(reqs) or pending:
+        now = time.perf_counter() - start
+        submitted = False
+        while i < len(reqs) and arrivals[i] <= now:
+            pending.append((srv.submit(reqs[i].mat, reqs[i].dtype), arrivals[i], reqs[i].n))
+            i += 1
+            submitted = True
+        rest = []
+        for k, (t, t_arr, n) in enumerate(pending):
+            state, _ = srv.poll(t)
+            if state == "done":
+                last = time.perf_counter() - start
+                lat.append(last - t_arr)
+                lat_n.append(n)
+            else:
+                rest.append((t, t_arr, n))
+                if fifo:
+                    rest.extend(pending[k + 1:])
+                    break
+        pending = rest
+        if now > limit_s:
+            break
+        if not submitted:
+            time.sleep(0.0002)
+    return np.array(lat), np.array(lat_n), last
+
+
+def pct(x, q):
+    return float(np.percentile(x, q) * 1e3) if len(x) else None
+
+
+def plain_rate(lp, reqs, limit_s):
+    """Plain per-request launches: one blocking perm_batch_host call per request
+    (PERM_FLAG_PLAIN plans, the default method choice), back to back."""
+    plans = {}
+    out = {"c128": np.zeros(2, dtype=np.float64), "u01": np.zeros(2, dtype=np.int64)}
+    st = np.zeros(1, dtype=np.int32)
+    lat = []
+    try:
+        start = time.perf_counter()
+        for r in reqs:
+            if r.dtype not in plans:
+                plans[r.dtype] = lp.Plan(36, r.dtype, flags=lp.FLAG_PLAIN, max_batch=1)
+            a = np.ascontiguousarray(r.mat, dtype=np.complex128 if r.dtype == "c128" else np.int64)
+            t0 = time.perf_counter()
+            plans[r.dtype].batch_host(a.reshape(-1), [a.shape[0]], out[r.dtype], st)
+            lat.append(time.perf_counter() - t0)
+            if time.perf_counter() - start > limit_s:
+                break
+        elapsed = time.perf_counter() - start
+    finally:
+        for p in plans.values():
+            p.close()
+    return len(lat) / elapsed, len(lat)
+
+
+def measure_serving_n20(lp, count=4096, poisson_s=2.0):
+    """The headline serving comparison: n = 20 complex requests (the batched
+    workload's matrices) served by the server vs plain per-request launches.
+    Saturated: all `count` requests submitted at once, permanents/s = count over
+    the time to the last completion.  Plain: one blocking perm_batch_host per
+    request (PERM_FLAG_PLAIN) on a sample.  Then Poisson arrivals at 0.8 x the
+    saturated rate for `poisson_s` seconds: p50/p90/p99 latency."""
+    from paper_1802_02779_gb300 import workloads as wl
+    cm, _ = wl.batched_n20(count=count)
+    reqs = [wl.Request(20, "c128", cm[i]) for i in range(count)]
+    with lp.Server() as srv:
+        drive_server(srv, reqs[:256], np.zeros(256), 60.0, fifo=True)          # warm-up
+        lat, _, last = drive_server(srv, reqs, np.zeros(count), 120.0, fifo=True)
+        served = count / last
+        rate = 0.8 * served
+        g = np.random.default_rng(wl.SEED_BASE + 10)
+        arr = np.cumsum(g.exponential(1.0 / rate, size=int(rate * poisson_s * 1.2) + 16))
+        arr = arr[arr < poisson_s]
+        preqs = [reqs[k % count] for k in range(len(arr))]
+        plat, _, plast = drive_server(srv, preqs, arr, poisson_s + 60.0, fifo=True)
+    plain, nplain = plain_rate(lp, reqs[:256], 30.0)
+    return {"requests": count, "served_perm_per_s": served, "plain_perm_per_s": plain,
+            "served_vs_plain": served / plain, "plain_sample": nplain,
+            "saturated_p50_ms": pct(lat, 50), "saturated_p99_ms": pct(lat, 99),
+            "poisson": {"rate_per_s": rate, "requests": int(len(arr)), "completed": int(len(plat)),
+                        "perm_per_s": float(len(plat) / plast) if plast else None,
+                        "p50_ms": pct(plat, 50), "p90_ms": pct(plat, 90), "p99_ms": pct(plat, 99)},
+            "how": "server: perm_submit / perm_poll from one host thread; plain: one blocking "
+                   "perm_batch_host per request (PERM_FLAG_PLAIN)"}
+
+
+def measure_serving(lp, requests=120, window_s=45.0):
+    """The mixed serving workload: n uniform in 10..36, 70% complex Haar
+    submatrices, 30% 0/1.  (1) Saturated: the first `requests` requests of the
+    stream all submitted at once, served vs plain per-request launches on the same
+    requests, permanents/s = requests over the time to the last completion.
+    (2) Poisson arrivals for `window_s` seconds at 0.8 x the saturated served rate:
+    latency = completion seen by perm_poll minus the scheduled arrival, and the
+    same arrival trace through plain per-request calls."""
     from paper_1802_02779_gb300 import workloads as wl
     pool = wl.uneven_requests(count=2000, seed=wl.SEED_BASE + 8, n_lo=10, n_hi=36)
-    u = wl.haar_unitary(256, wl.SEED_BASE + 7)
-    gcal = np.random.default_rng(wl.SEED_BASE + 9)
-    calib = [np.ascontiguousarray(u[:n][:, np.sort(gcal.choice(256, size=n, replace=False))])
-             for n in range(10, 37)]
+    sat = pool[:requests]
     with lp.Server() as srv:
-        t0 = time.perf_counter()
-        tk = [srv.submit(m, "c128") for m in calib]
-        srv.wait_all(tk, timeout_s=900)
-        capacity = len(calib) / (time.perf_counter() - t0)
-        rate = 0.8 * capacity
+        lat, lat_n, last = drive_server(srv, sat, np.zeros(len(sat)), 900.0)
+        served = len(lat) / last
+        rate = 0.8 * served
         g = np.random.default_rng(wl.SEED_BASE + 8)
         arrivals = np.cumsum(g.exponential(1.0 / rate, size=len(pool)))
-        arrivals = arrivals[arrivals < arrival_window_s]
-        reqs = pool[:len(arrivals)]
-        pending = {}
-        lat, lat_n = [], []
-        start = time.perf_counter()
-        i = 0
-        while i < len(reqs) or pending:
-            now = time.perf_counter() - start
-            while i < len(reqs) and arrivals[i] <= now:
-                pending[srv.submit(reqs[i].mat, reqs[i].dtype)] = (arrivals[i], reqs[i].n)
-                i += 1
-            for t in list(pending):
-                state, _ = srv.poll(t)
-                if state == "done":
-                    t_arr, n_req = pending.pop(t)
-                    lat.append(time.perf_counter() - start - t_arr)
-                    lat_n.append(n_req)
-            if now > arrival_window_s + drain_s:
-                break
-            time.sleep(0.0005)
-        elapsed = time.perf_counter() - start
-    lat = np.array(lat)
-    plain = serve_plain(lp, reqs, arrivals, arrival_window_s + drain_s)
-    return {"arrival_rate_per_s": rate, "capacity_per_s": capacity, "requests": int(len(reqs)),
-            "completed": int(len(lat)), "p50_ms": float(np.percentile(lat, 50) * 1e3) if len(lat) else None,
-            "p99_ms": float(np.percentile(lat, 99) * 1e3) if len(lat) else None,
-            "perm_per_s": float(len(lat) / elapsed), "n_range": [10, 36],
-            **latency_split(lat, np.array(lat_n)),
-            "calibration": "one complex request of each n = 10..36 served back to back",
-            "table_budget": "server default (min(80 GB, free/3))",
-            "plain": plain}
+        arrivals = arrivals[arrivals < window_s]
+        preqs = pool[requests:requests + len(arrivals)]
+        plat, plat_n, plast = drive_server(srv, preqs, arrivals, window_s + 120.0)
+    plain_sat, _ = plain_rate(lp, sat, 900.0)
+    plain = serve_plain(lp, preqs, arrivals, window_s + 120.0)
+    return {"n_range": [10, 36], "table_budget": "server default (min(80 GB, free/3))",
+            "saturated": {"requests": len(sat), "served_perm_per_s": served, "plain_perm_per_s": plain_sat,
+                          "served_vs_plain": served / plain_sat,
+                          "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99)},
+            "poisson": {"arrival_rate_per_s": rate, "requests": int(len(preqs)), "completed": int(len(plat)),
+                        "perm_per_s": float(len(plat) / plast) if plast else None,
+                        "p50_ms": pct(plat, 50), "p90_ms": pct(plat, 90), "p99_ms": pct(plat, 99),
+                        **latency_split(plat, plat_n), "plain": plain}}
 
 
 def latency_split(lat, ns):

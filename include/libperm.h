@@ -168,10 +168,9 @@ perm_status perm_batch_host(perm_plan_t plan, const void *mats, const int *sizes
                             void *out, int *item_status, void *stream);
 
 /* Continuous-batching server (one device; the server owns its streams, and
-   `stream` is ignored).  Requests of any n and
-   dtype are admitted while their Store-zechin tables fit the memory budget
-   (otherwise they run with Ryser), batched with whatever else is waiting, and
-   completed asynchronously.
+   `stream` is ignored).  Requests of any n and dtype are queued, batched with
+   whatever else is waiting, and completed asynchronously; work of different
+   requests overlaps on the device.
      perm_submit copies the host matrix (n*n elements of `dtype`) and returns a
        ticket; PERM_EAGAIN if the queue is full.
      perm_poll returns PERM_EAGAIN until the ticket is done, then writes the 16
@@ -182,12 +181,20 @@ perm_status perm_batch_host(perm_plan_t plan, const void *mats, const int *sizes
        does not finish within timeout_ms (the server is then left to drain in
        the background and its memory is not freed; at process exit its worker
        thread is stopped and joined before the CUDA runtime shuts down).
-   Server options: mem_budget_bytes = Store-zechin table budget of the large
-   lane (0 = min(80 GB, a third of the free memory)); max_batch = queue
+   Three lanes, by cost, each on streams of its own priority:
+     - complex n <= 20 and integer n <= 28: one batch of every pending request
+       as soon as the previous batch is done (highest priority);
+     - complex 21 <= n <= 34 whose Store-zechin tables fit mem_budget_bytes:
+       up to four jobs at once (a job: requests of one order, up to 16),
+       admitted while the tables of all jobs in flight fit the budget; the
+       tables come from a pool of the budget's size and return to it as each
+       job finishes;
+     - every other request with Ryser, batches of up to 64 (lowest priority).
+   Server options: mem_budget_bytes = Store-zechin table budget (0 = min(80 GB,
+   a third of the free memory), reserved at creation); max_batch = queue
    capacity (0 = 65536); flags: PERM_FLAG_WIDE as for plans; the other fields
-   are ignored.  Orders n <= 20 are batched together; larger complex orders run
-   one at a time, with Store-zechin when their tables fit the budget and with
-   Ryser otherwise; larger integer orders run with Ryser. */
+   are ignored.  Every result is the bits perm_batch gives for that matrix
+   (PERM_METHOD_AUTO; PERM_METHOD_RYSER for the Ryser lane). */
 perm_status perm_server_create(const perm_opts *opts, void *stream, perm_server_t *out);
 perm_status perm_submit(perm_server_t server, const void *host_mat, int n, perm_dtype dtype,
                         uint64_t *ticket);

@@ -1,24 +1,32 @@
 // server.cu -- continuous-batching permanent server (host side).
 //
 // Requests of any order and element type arrive through perm_submit and are
-// completed asynchronously.  A worker thread drives three lanes, each with its
-// own CUDA stream, so their work overlaps on the device:
+// completed asynchronously.  A worker thread drives three lanes on their own
+// CUDA streams, so their work overlaps on the device:
 //
-//   batch lane  orders n <= kSmallN: every pending request of this kind is
-//               taken into the next batch as soon as the previous batch of the
-//               lane has finished (continuous batching); complex matrices by
-//               Store-zechin with one CTA per matrix, integers by Ryser.
+//   fast lane   complex orders n <= 20 (Store-zechin, one CTA per matrix or
+//               the layer path) and integer orders n <= 28 (Ryser): every
+//               pending request of this kind joins the next batch as soon as
+//               the lane's previous batch has finished (continuous batching).
 //               Highest stream priority.
-//   table lane  complex orders n > kSmallN whose Store-zechin chain tables
-//               (the "stored sub-permanents" of Section 4 of Su & Zheng,
-//               arXiv:1802.02779) fit the table budget: admitted one at a
-//               time into the budget.  Middle priority.
-//   Ryser lane  the other orders n > kSmallN (and every larger integer
-//               order): Ryser's formula (Section 3.3), which needs no
-//               tables.  Lowest priority.
+//   table lane  complex orders 21..34 whose Store-zechin chain tables (the
+//               "stored sub-permanents" of Section 4 of Su & Zheng,
+//               arXiv:1802.02779) fit the table budget.  Up to kTableSlots
+//               jobs run at once, each on its own stream; a job is the request
+//               at the head of the queue plus the queued requests of the same
+//               order behind it (they share every layer launch).  A job is
+//               admitted while the tables of all jobs in flight stay within
+//               the budget -- C(t, t/2) chains of 2^13 entries, two layers,
+//               per matrix -- and its tables come from a stream-ordered memory
+//               pool and return to it when the job's kernels finish, so the
+//               next job is admitted as memory frees up.  Middle priority.
+//   Ryser lane  every other order (Ryser's formula, Section 3.3, which needs no
+//               tables): batches of pending requests, grouped by order inside
+//               one perm_batch, bounded by their number of Gray codes.  Lowest
+//               priority.
 //
 // The large lanes launch one CTA per chain or per piece of Gray codes, so
-// their CTAs retire every few milliseconds and a batch that arrives on the
+// their CTAs retire every few milliseconds and a batch that arrives on a
 // higher-priority lane takes the freed SM slots first.  The worker never
 // blocks on the device: it polls events, so a stuck lane cannot hang the
 // host; perm_server_destroy waits at most timeout_ms.
@@ -45,10 +53,18 @@ perm_status plan_create_impl(int n_max, perm_dtype dtype, const perm_opts* opts,
 
 namespace {
 
-constexpr int kSmallN = 20;
+constexpr int kFastComplexN = 20;        // complex orders of the fast lane
+constexpr int kFastIntN = 28;            // integer orders of the fast lane (Ryser, <= 1 ms each)
 constexpr int kQueueCap = 1 << 16;
-constexpr int kLaneBatch = 4096;
-constexpr int kLargeLow = 13;      // chain width of the one-matrix Store-zechin path
+constexpr int kFastBatch = 4096;
+constexpr int kTableSlots = 4;           // table-lane jobs in flight at once
+constexpr int kTableJob = 16;            // requests of one order per table job
+constexpr int kTableLow = 13;            // chain width of the one-matrix Store-zechin path
+constexpr int kRyserBatch = 64;
+constexpr double kRyserBatchCodes = 34359738368.0;   // 2^35 Gray codes per Ryser batch (>= 1 request)
+constexpr size_t kResultSlot = 32;       // bytes reserved per result in the slot buffers
+
+enum { kLaneFast = 0, kLaneTable = 1, kLaneRyser = 2, kLanes = 3 };
 
 struct Request {
     uint64_t ticket = 0;
@@ -64,16 +80,11 @@ struct Request {
 size_t elem_bytes(int dtype) { return dtype == PERM_C128 ? 16 : 8; }
 int dtype_slot(int dtype) { return dtype == PERM_C128 ? 0 : (dtype == PERM_U01 ? 1 : 2); }
 
-struct Lane {
+// One unit of work in flight: its stream, completion event and buffers.
+struct Slot {
     cudaStream_t stream = nullptr;
-    int priority = 0;
-    int method = PERM_METHOD_AUTO;
     cudaEvent_t done = nullptr;
-    perm_plan_t plans[3] = {nullptr, nullptr, nullptr};   // by dtype slot
-    int n_max = 0;
-    void* ext_ws = nullptr;          // large lane: shared Store-zechin workspace
-    size_t ext_ws_bytes = 0;
-    unsigned char* h_in = nullptr;   // pinned staging of one batch's inputs
+    unsigned char* h_in = nullptr;   // pinned staging of the inputs
     unsigned char* d_in = nullptr;
     size_t in_cap = 0;
     unsigned char* h_out = nullptr;  // pinned results (up to 32 B each) and statuses
@@ -81,29 +92,44 @@ struct Lane {
     int* h_status = nullptr;
     int* d_status = nullptr;
     int out_cap = 0;
+    ItemDesc* h_desc = nullptr;      // table slots: descriptors of the job's matrices
+    ItemDesc* d_desc = nullptr;
+    size_t ws_bytes = 0;             // table slots: bytes of the job's tables (budget accounting)
     std::vector<Request*> inflight;
     std::vector<size_t> inflight_at;  // byte offset of each in-flight result in h_out
-    std::atomic<bool> busy{false};
+    bool busy = false;
 };
 
-constexpr size_t kResultSlot = 32;   // bytes reserved per result in the lane buffers
+struct Lane {
+    int priority = 0;
+    int method = PERM_METHOD_AUTO;
+    int max_batch = 1;
+    perm_plan_t plans[3] = {nullptr, nullptr, nullptr};   // by dtype slot (fast and Ryser lanes)
+    int n_max[3] = {0, 0, 0};
+    std::vector<Slot> slots;
+};
 
 }  // namespace
 
 struct perm_server_s {
     perm_opts opts{};
+    int device = 0;
+    int num_sms = 0;
     std::mutex mu;
     std::condition_variable cv;
-    std::deque<Request*> queues[3];
+    std::deque<Request*> queues[kLanes];
     std::unordered_map<uint64_t, std::unique_ptr<Request>> reqs;
     uint64_t next_ticket = 1;
     int queued = 0;
     std::atomic<bool> stop{false};
     std::atomic<bool> failed{false};
     std::atomic<bool> abandon{false};   // process exit: the worker stops touching the device
+    std::atomic<int> busy_slots{0};
     std::thread worker;
-    Lane lanes[3];
+    Lane lanes[kLanes];
     size_t table_budget = 0;
+    size_t table_in_use = 0;            // tables of the table jobs in flight (worker thread only)
+    cudaMemPool_t pool = nullptr;       // stream-ordered pool of the table lane
     int queue_cap = kQueueCap;
 };
 
@@ -131,67 +157,85 @@ void stop_leaked_workers() {
     }
 }
 
-bool lane_alloc(Lane& L, size_t in_cap, int out_cap) {
-    if (cudaStreamCreateWithPriority(&L.stream, cudaStreamNonBlocking, L.priority) != cudaSuccess) return false;
-    if (cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming) != cudaSuccess) return false;
-    L.in_cap = in_cap;
-    L.out_cap = out_cap;
-    if (cudaMallocHost(&L.h_in, in_cap) != cudaSuccess) return false;
-    if (cudaMalloc(&L.d_in, in_cap) != cudaSuccess) return false;
-    if (cudaMallocHost(&L.h_out, (size_t)out_cap * kResultSlot) != cudaSuccess) return false;
-    if (cudaMalloc(&L.d_out, (size_t)out_cap * kResultSlot) != cudaSuccess) return false;
-    if (cudaMallocHost(&L.h_status, (size_t)out_cap * sizeof(int)) != cudaSuccess) return false;
-    if (cudaMalloc(&L.d_status, (size_t)out_cap * sizeof(int)) != cudaSuccess) return false;
+bool slot_alloc(Slot& S, int priority, size_t in_cap, int out_cap, int descs) {
+    if (cudaStreamCreateWithPriority(&S.stream, cudaStreamNonBlocking, priority) != cudaSuccess) return false;
+    if (cudaEventCreateWithFlags(&S.done, cudaEventDisableTiming) != cudaSuccess) return false;
+    S.in_cap = in_cap;
+    S.out_cap = out_cap;
+    if (cudaMallocHost(&S.h_in, in_cap) != cudaSuccess) return false;
+    if (cudaMalloc(&S.d_in, in_cap) != cudaSuccess) return false;
+    if (cudaMallocHost(&S.h_out, (size_t)out_cap * kResultSlot) != cudaSuccess) return false;
+    if (cudaMalloc(&S.d_out, (size_t)out_cap * kResultSlot) != cudaSuccess) return false;
+    if (cudaMallocHost(&S.h_status, (size_t)out_cap * sizeof(int)) != cudaSuccess) return false;
+    if (cudaMalloc(&S.d_status, (size_t)out_cap * sizeof(int)) != cudaSuccess) return false;
+    if (descs > 0) {
+        if (cudaMallocHost(&S.h_desc, (size_t)descs * sizeof(ItemDesc)) != cudaSuccess) return false;
+        if (cudaMalloc(&S.d_desc, (size_t)descs * sizeof(ItemDesc)) != cudaSuccess) return false;
+    }
     return true;
+}
+
+void slot_free(Slot& S) {
+    if (S.d_in) cudaFree(S.d_in);
+    if (S.d_out) cudaFree(S.d_out);
+    if (S.d_status) cudaFree(S.d_status);
+    if (S.d_desc) cudaFree(S.d_desc);
+    if (S.h_in) cudaFreeHost(S.h_in);
+    if (S.h_out) cudaFreeHost(S.h_out);
+    if (S.h_status) cudaFreeHost(S.h_status);
+    if (S.h_desc) cudaFreeHost(S.h_desc);
+    if (S.done) cudaEventDestroy(S.done);
+    if (S.stream) cudaStreamDestroy(S.stream);
+    S = Slot();
 }
 
 void lane_free(Lane& L) {
     for (auto& p : L.plans)
         if (p) { perm_plan_destroy(p); p = nullptr; }
-    if (L.ext_ws) cudaFree(L.ext_ws);
-    if (L.d_in) cudaFree(L.d_in);
-    if (L.d_out) cudaFree(L.d_out);
-    if (L.d_status) cudaFree(L.d_status);
-    if (L.h_in) cudaFreeHost(L.h_in);
-    if (L.h_out) cudaFreeHost(L.h_out);
-    if (L.h_status) cudaFreeHost(L.h_status);
-    if (L.done) cudaEventDestroy(L.done);
-    if (L.stream) cudaStreamDestroy(L.stream);
-    L.stream = nullptr; L.done = nullptr; L.ext_ws = nullptr; L.d_in = nullptr; L.d_out = nullptr;
-    L.d_status = nullptr; L.h_in = nullptr; L.h_out = nullptr; L.h_status = nullptr;
-    L.inflight.clear();
-    L.inflight_at.clear();
-    L.busy = false;
+    for (auto& S : L.slots) slot_free(S);
+    L.slots.clear();
 }
 
-perm_plan_t lane_plan(perm_server_t s, Lane& L, int dtype, bool large) {
+perm_plan_t lane_plan(perm_server_t s, Lane& L, int dtype) {
     const int k = dtype_slot(dtype);
     if (!L.plans[k]) {
-        perm_opts o = s->opts;
+        perm_opts o{};
         o.flags = dtype == PERM_C128 ? 0u : (s->opts.flags & PERM_FLAG_WIDE);
         o.method = L.method;
-        o.max_batch = large ? 1 : kLaneBatch;
-        if (!large) o.mem_budget_bytes = 0;   // the table budget applies to the large lane
+        o.max_batch = L.max_batch;
         perm_plan_t p = nullptr;
-        perm_status st;
-        if (large && L.ext_ws)
-            st = plan_create_impl(L.n_max, (perm_dtype)dtype, &o, L.ext_ws, L.ext_ws_bytes, &p);
-        else
-            st = plan_create_impl(L.n_max, (perm_dtype)dtype, &o, nullptr, 0, &p);
-        if (st != PERM_OK) return nullptr;
+        if (plan_create_impl(L.n_max[k], (perm_dtype)dtype, &o, nullptr, 0, &p) != PERM_OK) return nullptr;
         L.plans[k] = p;
     }
     return L.plans[k];
 }
 
-// Launch the requests `batch` (all of one lane) on the lane's stream.
-bool lane_launch(perm_server_t s, Lane& L, std::vector<Request*>& batch, bool large) {
-    // group by dtype: one perm_batch per dtype, inputs packed per group; each group's
-    // results are packed at its own slot size (16 B, or 32 B for wide integers)
+// Table bytes of one complex matrix of order n on the table lane.
+size_t table_bytes(int n) { return sz_matrix_workspace_bytes(PERM_C128, n, kTableLow); }
+
+// Gray codes Ryser walks for one request (the Ryser lane's batch bound).
+double ryser_codes(const Request* r) {
+    return std::ldexp(1.0, r->dtype == PERM_I64 ? r->n : std::max(0, r->n - 1));
+}
+
+// Copy results back and record the slot's completion event.
+bool slot_finish_launch(Slot& S, size_t out_bytes, int nout) {
+    if (cudaMemcpyAsync(S.h_out, S.d_out, out_bytes, cudaMemcpyDeviceToHost, S.stream) != cudaSuccess)
+        return false;
+    if (cudaMemcpyAsync(S.h_status, S.d_status, (size_t)nout * sizeof(int), cudaMemcpyDeviceToHost,
+                        S.stream) != cudaSuccess)
+        return false;
+    return cudaEventRecord(S.done, S.stream) == cudaSuccess;
+}
+
+// Fast and Ryser lanes: the requests `batch` through the lane's plans, one
+// perm_batch per dtype, inputs packed per dtype group; each group's results are
+// packed at its own slot size (16 B, or 32 B for wide integers).
+bool plan_launch(perm_server_t s, Lane& L, Slot& S, std::vector<Request*>& batch) {
     size_t off = 0, out_off = 0;
     int outpos = 0;
-    L.inflight.clear();
-    L.inflight_at.clear();
+    S.inflight.clear();
+    S.inflight_at.clear();
     for (int slot = 0; slot < 3; slot++) {
         const int dtype = slot == 0 ? PERM_C128 : (slot == 1 ? PERM_U01 : PERM_I64);
         const size_t rbytes = (dtype != PERM_C128 && (s->opts.flags & PERM_FLAG_WIDE)) ? 32 : 16;
@@ -201,63 +245,147 @@ bool lane_launch(perm_server_t s, Lane& L, std::vector<Request*>& batch, bool la
         const int status_start = outpos;
         for (Request* r : batch) {
             if (r->dtype != dtype) continue;
-            std::memcpy(L.h_in + off, r->mat.data(), r->mat.size());
+            std::memcpy(S.h_in + off, r->mat.data(), r->mat.size());
             off += r->mat.size();
             sizes.push_back(r->n);
             r->result_bytes = (int)rbytes;
-            L.inflight.push_back(r);
-            L.inflight_at.push_back(out_off);
+            S.inflight.push_back(r);
+            S.inflight_at.push_back(out_off);
             out_off += rbytes;
             outpos++;
         }
         if (sizes.empty()) continue;
-        perm_plan_t p = lane_plan(s, L, dtype, large);
+        perm_plan_t p = lane_plan(s, L, dtype);
         if (!p) return false;
-        if (cudaMemcpyAsync(L.d_in + start, L.h_in + start, off - start, cudaMemcpyHostToDevice,
-                            L.stream) != cudaSuccess)
+        if (off > start && cudaMemcpyAsync(S.d_in + start, S.h_in + start, off - start,
+                                           cudaMemcpyHostToDevice, S.stream) != cudaSuccess)
             return false;
-        if (perm_batch(p, L.d_in + start, sizes.data(), (int)sizes.size(), L.d_out + out_start,
-                       L.d_status + status_start, L.stream) != PERM_OK)
+        if (perm_batch(p, S.d_in + start, sizes.data(), (int)sizes.size(), S.d_out + out_start,
+                       S.d_status + status_start, S.stream) != PERM_OK)
             return false;
     }
-    // results back in the same order (dtype groups)
-    if (cudaMemcpyAsync(L.h_out, L.d_out, out_off, cudaMemcpyDeviceToHost, L.stream) != cudaSuccess)
-        return false;
-    if (cudaMemcpyAsync(L.h_status, L.d_status, (size_t)outpos * sizeof(int), cudaMemcpyDeviceToHost,
-                        L.stream) != cudaSuccess)
-        return false;
-    if (cudaEventRecord(L.done, L.stream) != cudaSuccess) return false;
+    if (!slot_finish_launch(S, out_off, outpos)) return false;
     for (Request* r : batch) r->state.store(1, std::memory_order_relaxed);
-    L.busy = true;
+    S.busy = true;
     return true;
 }
 
-void lane_complete(Lane& L) {
-    for (size_t i = 0; i < L.inflight.size(); i++) {
-        Request* r = L.inflight[i];
-        std::memcpy(r->result, L.h_out + L.inflight_at[i], (size_t)r->result_bytes);
-        r->status = L.h_status[i];
+// Table lane: one job (requests of one order) on the slot's stream, its tables
+// from the pool on the same stream and released behind the job's kernels.
+// Returns 1 on success, 0 if the tables could not be allocated (nothing was
+// launched), -1 on a CUDA error.
+int table_launch(perm_server_t s, Slot& S, std::vector<Request*>& job) {
+    const int n = job[0]->n;
+    const int c = (int)job.size();
+    const size_t ws_item = table_bytes(n);
+    S.inflight.clear();
+    S.inflight_at.clear();
+    size_t off = 0;
+    for (int i = 0; i < c; i++) {
+        Request* r = job[i];
+        std::memcpy(S.h_in + off, r->mat.data(), r->mat.size());
+        S.h_desc[i] = ItemDesc{(long long)(off / 16), n, i};
+        off += r->mat.size();
+        r->result_bytes = 16;
+        S.inflight.push_back(r);
+        S.inflight_at.push_back((size_t)i * 16);
+    }
+    void* ws = nullptr;
+    if (cudaMallocFromPoolAsync(&ws, (size_t)c * ws_item, s->pool, S.stream) != cudaSuccess) {
+        cudaGetLastError();
+        S.inflight.clear();
+        S.inflight_at.clear();
+        return 0;
+    }
+    bool ok = cudaMemcpyAsync(S.d_in, S.h_in, off, cudaMemcpyHostToDevice, S.stream) == cudaSuccess &&
+              cudaMemcpyAsync(S.d_desc, S.h_desc, (size_t)c * sizeof(ItemDesc), cudaMemcpyHostToDevice,
+                              S.stream) == cudaSuccess;
+    if (ok)
+        ok = sz_launch_layers(PERM_C128, S.d_in, S.d_desc, c, n, kTableLow, S.d_out, 2, S.d_status, ws, ws_item,
+                              2 * s->num_sms, S.stream) == cudaSuccess;
+    if (cudaFreeAsync(ws, S.stream) != cudaSuccess) ok = false;
+    if (ok) ok = slot_finish_launch(S, (size_t)c * 16, c);
+    if (!ok) return -1;
+    for (Request* r : job) r->state.store(1, std::memory_order_relaxed);
+    S.ws_bytes = (size_t)c * ws_item;
+    S.busy = true;
+    return 1;
+}
+
+void slot_complete(Slot& S) {
+    for (size_t i = 0; i < S.inflight.size(); i++) {
+        Request* r = S.inflight[i];
+        std::memcpy(r->result, S.h_out + S.inflight_at[i], (size_t)r->result_bytes);
+        r->status = S.h_status[i];
         r->state.store(2, std::memory_order_release);
     }
-    L.inflight.clear();
-    L.inflight_at.clear();
-    L.busy = false;
+    S.inflight.clear();
+    S.inflight_at.clear();
+    S.busy = false;
+}
+
+void fail_requests(std::vector<Request*>& v) {
+    for (Request* r : v) { r->status = PERM_ECUDA; r->state.store(2, std::memory_order_release); }
+}
+
+// Take requests for the fast or the Ryser lane (caller holds s->mu).
+void take_batch(perm_server_t s, int li, const Slot& S, std::vector<Request*>& batch) {
+    auto& q = s->queues[li];
+    size_t bytes = 0;
+    double codes = 0.0;
+    const size_t cap = li == kLaneFast ? (size_t)kFastBatch : (size_t)kRyserBatch;
+    while (!q.empty() && batch.size() < cap && batch.size() < (size_t)S.out_cap) {
+        Request* r = q.front();
+        if (bytes + r->mat.size() > S.in_cap) break;
+        if (li == kLaneRyser && !batch.empty() && codes + ryser_codes(r) > kRyserBatchCodes) break;
+        bytes += r->mat.size();
+        codes += ryser_codes(r);
+        batch.push_back(r);
+        q.pop_front();
+    }
+    s->queued -= (int)batch.size();
+}
+
+// Take one table job (caller holds s->mu): the head of the queue, if its tables
+// fit what the jobs in flight leave of the budget (first come, first served:
+// nothing overtakes a head that does not fit yet), plus queued requests of the
+// same order while their tables fit too.
+void take_table_job(perm_server_t s, std::vector<Request*>& job) {
+    auto& q = s->queues[kLaneTable];
+    if (q.empty()) return;
+    const int n = q.front()->n;
+    const size_t ws_item = table_bytes(n);
+    size_t used = s->table_in_use;
+    for (auto it = q.begin(); it != q.end() && (int)job.size() < kTableJob;) {
+        Request* r = *it;
+        if (r->n != n) { ++it; continue; }
+        if (used + ws_item > s->table_budget) break;
+        used += ws_item;
+        job.push_back(r);
+        it = q.erase(it);
+    }
+    s->queued -= (int)job.size();
 }
 
 void worker_loop(perm_server_t s) {
-    int dev = 0;
-    cudaGetDevice(&dev);
+    cudaSetDevice(s->device);
     std::vector<Request*> batch;
     while (true) {
         if (s->abandon.load()) break;
         bool did = false;
         // completions
-        for (int li = 0; li < 3; li++) {
-            Lane& L = s->lanes[li];
-            if (L.busy) {
-                const cudaError_t q = cudaEventQuery(L.done);
-                if (q == cudaSuccess) { lane_complete(L); did = true; }
-                else if (q != cudaErrorNotReady) { s->failed = true; }
+        for (int li = 0; li < kLanes; li++) {
+            for (Slot& S : s->lanes[li].slots) {
+                if (!S.busy) continue;
+                const cudaError_t q = cudaEventQuery(S.done);
+                if (q == cudaSuccess) {
+                    slot_complete(S);
+                    if (li == kLaneTable) { s->table_in_use -= S.ws_bytes; S.ws_bytes = 0; }
+                    s->busy_slots--;
+                    did = true;
+                } else if (q != cudaErrorNotReady) {
+                    s->failed = true;
+                }
             }
         }
         if (s->failed.load()) {
@@ -269,37 +397,47 @@ void worker_loop(perm_server_t s) {
             }
             s->queued = 0;
         }
-        // new batches
-        for (int li = 0; li < 3; li++) {
+        // new work, highest priority first
+        for (int li = 0; li < kLanes && !s->failed.load(); li++) {
             Lane& L = s->lanes[li];
-            if (L.busy || s->failed) continue;
-            batch.clear();
-            {
-                std::lock_guard<std::mutex> g(s->mu);
-                auto& q = s->queues[li];
-                size_t bytes = 0;
-                const size_t max_items = li == 0 ? (size_t)kLaneBatch : 1;
-                while (!q.empty() && batch.size() < max_items) {
-                    Request* r = q.front();
-                    if (bytes + r->mat.size() > L.in_cap) break;
-                    bytes += r->mat.size();
-                    batch.push_back(r);
-                    q.pop_front();
+            for (Slot& S : L.slots) {
+                if (S.busy || s->failed.load()) continue;
+                batch.clear();
+                {
+                    std::lock_guard<std::mutex> g(s->mu);
+                    if (li == kLaneTable) take_table_job(s, batch);
+                    else take_batch(s, li, S, batch);
                 }
-                s->queued -= (int)batch.size();
-            }
-            if (!batch.empty()) {
-                if (!lane_launch(s, L, batch, li != 0)) {
-                    s->failed = true;
-                    for (Request* r : batch) { r->status = PERM_ECUDA; r->state.store(2, std::memory_order_release); }
-                }
+                if (batch.empty()) break;      // nothing (more) this lane can start now
                 did = true;
+                if (li == kLaneTable) {
+                    const int rc = table_launch(s, S, batch);
+                    if (rc == 1) {
+                        s->table_in_use += S.ws_bytes;
+                        s->busy_slots++;
+                    } else if (rc == 0) {
+                        // the pool could not supply the tables: these requests run with Ryser
+                        std::lock_guard<std::mutex> g(s->mu);
+                        for (auto it = batch.rbegin(); it != batch.rend(); ++it)
+                            s->queues[kLaneRyser].push_front(*it);
+                        s->queued += (int)batch.size();
+                        break;
+                    } else {
+                        s->failed = true;
+                        fail_requests(batch);
+                    }
+                } else if (plan_launch(s, L, S, batch)) {
+                    s->busy_slots++;
+                } else {
+                    s->failed = true;
+                    fail_requests(batch);
+                }
             }
         }
-        const bool idle = !s->lanes[0].busy && !s->lanes[1].busy && !s->lanes[2].busy;
+        const bool idle = s->busy_slots.load() == 0;
         if (s->stop.load() && idle) {
             std::lock_guard<std::mutex> g(s->mu);
-            if (s->queues[0].empty() && s->queues[1].empty() && s->queues[2].empty()) break;
+            if (s->queued == 0) break;
         }
         if (s->stop.load() && s->failed.load()) break;
         if (!did) {
@@ -314,47 +452,76 @@ void worker_loop(perm_server_t s) {
 extern "C" {
 
 perm_status perm_server_create(const perm_opts* opts, void* stream, perm_server_t* out) {
-    (void)stream;   // the server owns one stream per lane
+    (void)stream;   // the server owns its streams
     if (!out) return PERM_EINVAL;
     *out = nullptr;
     perm_server_t s = new (std::nothrow) perm_server_s();
     if (!s) return PERM_ENOMEM;
     if (opts) s->opts = *opts;
     if (s->opts.max_batch > 0) s->queue_cap = s->opts.max_batch;
-    // table budget for the large lane: default 20 GB (or what is free)
     size_t free_b = 0, total_b = 0;
-    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) { delete s; return PERM_ECUDA; }
+    if (cudaGetDevice(&s->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device) != cudaSuccess ||
+        cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        delete s;
+        return PERM_ECUDA;
+    }
+    // table budget of the table lane: default min(80 GB, a third of the free memory)
     s->table_budget = s->opts.mem_budget_bytes ? s->opts.mem_budget_bytes
                                                : std::min<size_t>((size_t)80 << 30, free_b / 3);
     int least = 0, greatest = 0;
     cudaDeviceGetStreamPriorityRange(&least, &greatest);
-    Lane& small = s->lanes[0];
-    Lane& large = s->lanes[1];
-    Lane& ryser = s->lanes[2];
-    small.n_max = kSmallN;
-    small.priority = greatest;
-    large.n_max = kMaxNSZ;
-    large.priority = (least + greatest) / 2;
-    ryser.n_max = kMaxN;
+    Lane& fast = s->lanes[kLaneFast];
+    Lane& table = s->lanes[kLaneTable];
+    Lane& ryser = s->lanes[kLaneRyser];
+    fast.priority = greatest;
+    fast.max_batch = kFastBatch;
+    fast.n_max[0] = kFastComplexN;
+    fast.n_max[1] = fast.n_max[2] = kFastIntN;
+    table.priority = (least + greatest) / 2;
     ryser.priority = least;
     ryser.method = PERM_METHOD_RYSER;
-    bool ok = lane_alloc(small, (size_t)kLaneBatch * kSmallN * kSmallN * 16, kLaneBatch) &&
-              lane_alloc(large, (size_t)kMaxN * kMaxN * 16, 1) &&
-              lane_alloc(ryser, (size_t)kMaxN * kMaxN * 16, 1);
+    ryser.max_batch = kRyserBatch;
+    ryser.n_max[0] = ryser.n_max[1] = ryser.n_max[2] = kMaxN;
+    fast.slots.resize(1);
+    table.slots.resize(kTableSlots);
+    ryser.slots.resize(1);
+    const size_t fast_in = (size_t)kFastBatch * std::max<size_t>(kFastComplexN * kFastComplexN * 16,
+                                                                 kFastIntN * kFastIntN * 8);
+    bool ok = slot_alloc(fast.slots[0], fast.priority, fast_in, kFastBatch, 0) &&
+              slot_alloc(ryser.slots[0], ryser.priority, (size_t)kRyserBatch * kMaxN * kMaxN * 16, kRyserBatch, 0);
+    for (Slot& S : table.slots)
+        if (ok) ok = slot_alloc(S, table.priority, (size_t)kTableJob * kMaxNSZ * kMaxNSZ * 16, kTableJob, kTableJob);
+    // the table lane's pool: memory stays reserved up to the budget (release threshold) and is
+    // reused by later jobs once the jobs that freed it are seen to be complete
     if (ok) {
-        large.ext_ws_bytes = s->table_budget;
-        ok = cudaMalloc(&large.ext_ws, large.ext_ws_bytes) == cudaSuccess;
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = s->device;
+        ok = cudaMemPoolCreate(&s->pool, &props) == cudaSuccess;
+        unsigned long long thr = s->table_budget;
+        int no = 0;
+        if (ok) ok = cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &thr) == cudaSuccess;
+        if (ok) ok = cudaMemPoolSetAttribute(s->pool, cudaMemPoolReuseAllowInternalDependencies, &no) == cudaSuccess;
+        // reserve the budget now: one allocation of all of it, returned to the pool
+        void* p = nullptr;
+        cudaStream_t st0 = table.slots[0].stream;
+        if (ok) ok = cudaMallocFromPoolAsync(&p, s->table_budget, s->pool, st0) == cudaSuccess;
+        if (ok) ok = cudaFreeAsync(p, st0) == cudaSuccess;
+        if (ok) ok = cudaStreamSynchronize(st0) == cudaSuccess;
     }
-    // every lane's plans now (they load their kernels): creating one, or loading a kernel,
-    // while another lane's work runs could wait for that work
+    // the plans now (they load their kernels): creating one, or loading a kernel, while another
+    // lane's work runs could wait for that work; the table lane's kernels are loaded here too
     for (int dt : {PERM_C128, PERM_U01, PERM_I64}) {
-        if (ok) ok = lane_plan(s, small, dt, false) != nullptr;
-        if (ok) ok = lane_plan(s, ryser, dt, true) != nullptr;
+        if (ok) ok = lane_plan(s, fast, dt) != nullptr;
+        if (ok) ok = lane_plan(s, ryser, dt) != nullptr;
     }
-    if (ok) ok = lane_plan(s, large, PERM_C128, true) != nullptr;   // the table lane takes complex requests
+    if (ok) ok = sz_init_tables() == cudaSuccess && sz_preload(PERM_C128) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         for (auto& L : s->lanes) lane_free(L);
+        if (s->pool) cudaMemPoolDestroy(s->pool);
         delete s;
         return PERM_ENOMEM;
     }
@@ -375,20 +542,19 @@ perm_status perm_submit(perm_server_t s, const void* host_mat, int n, perm_dtype
     const size_t bytes = (size_t)n * n * elem_bytes(dtype);
     r->mat.resize(bytes);
     if (bytes) std::memcpy(r->mat.data(), host_mat, bytes);
+    // lane by cost: small orders batch on the fast lane; complex orders whose Store-zechin
+    // tables fit the budget on the table lane; everything else with Ryser
+    int lane;
+    if (n <= (dtype == PERM_C128 ? kFastComplexN : kFastIntN)) lane = kLaneFast;
+    else if (auto_uses_sz(dtype) && n <= kMaxNSZ && table_bytes(n) + ((size_t)1 << 20) <= s->table_budget)
+        lane = kLaneTable;
+    else lane = kLaneRyser;
     {
         std::lock_guard<std::mutex> g(s->mu);
         if (s->queued >= s->queue_cap) return PERM_EAGAIN;
         r->ticket = s->next_ticket++;
         *ticket = r->ticket;
         Request* raw = r.get();
-        int lane = 0;
-        if (n > kSmallN) {
-            // complex: admission by table memory, Store-zechin if its chains fit the budget,
-            // else Ryser; integers: Ryser (the method PERM_METHOD_AUTO picks for them)
-            const bool fits = auto_uses_sz(dtype) && n <= kMaxNSZ &&
-                              sz_matrix_workspace_bytes(dtype, n, kLargeLow) + ((size_t)1 << 20) <= s->table_budget;
-            lane = fits ? 1 : 2;
-        }
         s->queues[lane].push_back(raw);
         s->queued++;
         s->reqs.emplace(raw->ticket, std::move(r));
@@ -422,8 +588,7 @@ perm_status perm_server_destroy(perm_server_t s, int timeout_ms) {
         bool busy;
         {
             std::lock_guard<std::mutex> g(s->mu);
-            busy = s->lanes[0].busy || s->lanes[1].busy || s->lanes[2].busy || !s->queues[0].empty() ||
-                   !s->queues[1].empty() || !s->queues[2].empty();
+            busy = s->busy_slots.load() > 0 || s->queued > 0;
         }
         if (!busy || s->failed.load()) break;
         if (std::chrono::steady_clock::now() >= deadline) { result = PERM_ETIMEDOUT; break; }
@@ -439,6 +604,7 @@ perm_status perm_server_destroy(perm_server_t s, int timeout_ms) {
     }
     s->worker.join();
     for (auto& L : s->lanes) lane_free(L);
+    if (s->pool) cudaMemPoolDestroy(s->pool);
     delete s;
     return result;
 }

@@ -103,3 +103,33 @@ print("RC", rc)
     assert r.returncode == 0, r.stderr
     from paper_1802_02779_gb300 import libperm as lp
     assert f"RC {lp.PERM_ETIMEDOUT}" in r.stdout
+
+
+def _uneven_large_complex(lp, orders):
+    """Large complex requests of the uneven stream with their stored oracle values."""
+    import json
+    from paper_1802_02779_gb300 import workloads as wl
+    with open(os.path.join(ROOT, "tests", "golden", "large_complex.json")) as f:
+        gold = json.load(f)
+    reqs = wl.uneven_requests(**gold["streams"]["uneven"])
+    cases = [c for c in gold["cases"] if c["stream"] == "uneven" and c["n"] in orders]
+    return [(reqs[c["index"]].mat, complex(*c["per"]), c["per_abs"]) for c in cases]
+
+
+@pytest.mark.parametrize("budget_mb", [8192, 700])
+def test_table_lane_concurrent_jobs_same_bits_as_alone(lp, budget_mb):
+    """Large complex requests of orders 23..26 submitted together: with an 8 GB
+    budget several table jobs are in flight at once (same-order requests share
+    layer launches); with 700 MB one order-26 job (675 MB of tables) fits at a
+    time and the others wait for its memory.  Every result is the bits
+    perm_batch gives the matrix alone and within the oracle's tolerance."""
+    cases = _uneven_large_complex(lp, (23, 24, 25, 26))
+    assert len(cases) >= 20
+    with lp.Server(mem_budget_bytes=budget_mb << 20) as srv:
+        tickets = [srv.submit(a, "c128") for a, _, _ in cases]
+        res = srv.wait_all(tickets, timeout_s=600)
+    for (a, want, scale), (val, st) in zip(cases, res):
+        assert st == lp.PERM_OK
+        alone = lp.permanents([a], "c128")[0]
+        assert val == alone, (a.shape[0], val, alone)
+        assert abs(val - want) <= 1e-12 * scale
