@@ -157,13 +157,13 @@ def sz_c128_flops(n: int) -> float:
     """FP64 flops the complex Store-zechin kernel executes per n x n permanent.
 
     Each term a[k-1][j] * T_{k-1}[S \\ j] of a level 2 <= k <= n-1 entry is three
-    FMAs (6 flops, three-multiplication complex form); each such entry adds 4
-    additions (Re = P1-P2, Im = P3-P1-P2, w = Re+Im).  Level 1 is a copy; the
+    FMAs (6 flops, three-multiplication complex form); each such entry adds 3
+    additions (Re = P1-P2, w = P3-2 P2, Im = w-Re).  Level 1 is a copy; the
     final level (n terms in double-double) is negligible and not counted."""
     from math import comb
     f = 0.0
     for k in range(2, n):
-        f += comb(n, k) * (6.0 * k + 4.0)
+        f += comb(n, k) * (6.0 * k + 3.0)
     return f
 
 
@@ -317,14 +317,19 @@ def run_gpu(args, rank, world):
         return
 
     c_kernel_ms = float(np.mean(c_ms))
-    flops = sz_c128_flops(N) * count
+    # achieved: the method's own work per permanent (n(2^(n-1)-1) complex multiplications at
+    # 6 flops, (n-2)2^(n-1)+1 complex additions at 2), the per-unit figure of the roofline
+    flops = sz_c128_standard_flops(N) * count
     achieved = flops / (c_kernel_ms / 1000.0) / 1e12
+    executed = sz_c128_flops(N) * count / (c_kernel_ms / 1000.0) / 1e12
     peak = fp64_peak / 1e12
     roofline = {"bound": "alu", "pipe": "fp64", "kernel": "sz_batched_c128",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "peak_source": "measured this run by perm_measure_fp64_peak (independent DFMA chains, all SMs)",
-                "work_per_permanent_flops": sz_c128_flops(N),
-                "standard_count_flops_per_permanent": sz_c128_standard_flops(N),
+                "work_per_permanent_flops": sz_c128_standard_flops(N),
+                "work_count": "the method's complex multiplications x 6 + complex additions x 2",
+                "executed_flops_per_permanent": sz_c128_flops(N),
+                "executed_tflops": executed, "executed_frac": executed / peak,
                 "traffic": traffic_per_launch(count),
                 "traffic_unit": "bytes per launch (ncu dram__bytes_read+write, scaled per matrix)"}
 

@@ -123,9 +123,9 @@ patterns_c128(const double2* __restrict__ mats, int count, int rows, int cols, d
                     P2 = __fma_rn(c.y, p.y, P2);
                     P3 = __fma_rn(rs[j], sw[pm], P3);
                 }
-                u = __fma_rn(P2, -1.0, P1);
-                v = __fma_rn(P2, -1.0, __fma_rn(P1, -1.0, P3));
-                w = __fma_rn(u, 1.0, v);
+                u = __fma_rn(P2, -1.0, P1);         // the epilogue of chain_c128
+                w = __fma_rn(P2, -2.0, P3);
+                v = __fma_rn(u, -1.0, w);
             }
             suv[mask] = make_double2(u, v);
             sw[mask] = w;

@@ -280,11 +280,12 @@ __device__ void chain_c128(const MatCtx& mc, int s, unsigned char* chain_smem, c
                     P2 = __fma_rn(c.y, p.y, P2);
                     P3 = __fma_rn(rs[j], pw, P3);
                 }
-                // Re = P1 - P2, Im = (P3 - P1) - P2, w = Re + Im, each a single
-                // rounding; written as FMAs with +-1 (same results, faster pipe issue)
+                // Re = P1 - P2 and w = Re + Im = P3 - 2 P2 (one rounding each),
+                // Im = w - Re: three FP64 operations, written as FMAs with
+                // constant factors (the pipe issues FMAs faster than adds)
                 u = __fma_rn(P2, -1.0, P1);
-                v = __fma_rn(P2, -1.0, __fma_rn(P1, -1.0, P3));
-                w = __fma_rn(u, 1.0, v);
+                w = __fma_rn(P2, -2.0, P3);
+                v = __fma_rn(u, -1.0, w);
             }
             suv[mask] = make_double2(u, v);
             sw[mask] = w;
