@@ -108,10 +108,14 @@ typedef enum perm_method {
                                  descriptor buffer, captures and instantiates a graph; later
                                  calls with the same signature only launch the graph (16 are
                                  cached per plan, least recently used evicted) */
-#define PERM_FLAG_AUTOTUNE 4u /* at plan creation, time every CTA size and chain width of the
-                                 batched Store-zechin kernel on a synthetic batch and keep the
-                                 fastest (results are bit-identical for every choice); cached
-                                 per process and in the file LIBPERM_TUNE_CACHE names, if set */
+#define PERM_FLAG_AUTOTUNE 4u /* at plan creation, time candidate launch shapes on synthetic
+                                 batches and keep the fastest: the batched Store-zechin kernel's
+                                 CTA size and chain width; for complex plans of n_max >= 21 also
+                                 the largest order run one CTA per matrix (19..22) and the layer
+                                 path's CTA size, chain width and CTAs per launch.  Results are
+                                 bit-identical for every choice; perm_plan_describe reports
+                                 them; cached per (device, dtype, n_max) for the process and in
+                                 the file LIBPERM_TUNE_CACHE names, if set */
 #define PERM_FLAG_WIDE 8u     /* integer plans only (PERM_EINVAL for PERM_C128): results are
                                  256-bit slots (four uint64 per matrix), and Ryser computes
                                  modulo 2^192, so every permanent whose bound is below 2^192 is

@@ -59,6 +59,9 @@ struct perm_plan_s {
     int num_sms = 0;
     int m_low = 12;               // chain width of the batched kernel (two CTAs per SM)
     int m_single = 13;            // chain width of the one-matrix-over-the-GPU path
+    int layer_threads = 512;      // CTA size of that path's complex kernel (384: two CTAs per SM)
+    int layer_grid_mult = 2;      // its CTAs per launch, in units of the SM count
+    bool tail_to_layers = true;   // the batched kernel's last partial round takes the layer path
     int c128_threads = 384;       // CTA size of the batched complex kernel
     int int_threads = 256;        // CTA size of the batched integer kernel
     int out_words = 2;            // integer result slot in 64-bit words (4 with PERM_FLAG_WIDE)
@@ -114,7 +117,7 @@ void release(T*& p) {
 
 perm_status cuda_status(cudaError_t e) { return e == cudaSuccess ? PERM_OK : PERM_ECUDA; }
 
-int sz_batch_limit(perm_plan_t p) {
+int sz_batch_limit(perm_plan_t p, int complex_cap = 20) {
     // One CTA per matrix when the per-CTA chain workspace stays <= 80 MB.  For complex
     // matrices at most n = 20: measured on GB300 (batches of 512-4096 matrices), the layer
     // path, with every same-order matrix in each layer launch, is 3-11% faster at n = 21-22,
@@ -124,7 +127,7 @@ int sz_batch_limit(perm_plan_t p) {
     for (int n = 1; n <= std::min(p->n_max, kMaxNSZ); n++) {
         if (sz_matrix_workspace_bytes(p->dtype, n, p->m_low) <= (size_t)80 << 20) best = n;
     }
-    if (p->dtype == PERM_C128) best = std::min(best, 20);
+    if (p->dtype == PERM_C128) best = std::min(best, complex_cap);
     return best;
 }
 
@@ -137,8 +140,12 @@ static perm_status plan_create_tuned(int n_max, perm_dtype dtype, const perm_opt
                                      perm_plan_t* out);
 // Kernel-shape choices of the autotuner (0 = default).
 struct PlanShape {
-    int m_low = 0;      // chain width of the batched kernel
-    int threads = 0;    // CTA size of the batched kernel
+    int m_low = 0;           // chain width of the batched kernel
+    int threads = 0;         // CTA size of the batched kernel
+    int batch_nmax = -1;     // largest complex order of the batched kernel (-1: 20)
+    int layer_threads = 0;   // CTA size of the layer path's complex kernel (384 or 512)
+    int m_single = 0;        // chain width of the layer path
+    int layer_grid_mult = 0; // CTAs per layer launch in units of the SM count
 };
 static perm_status plan_create_core(int n_max, perm_dtype dtype, const perm_opts* opts, void* ext_ws,
                                     size_t ext_ws_bytes, PlanShape shape, perm_plan_t* out);
@@ -197,9 +204,17 @@ static perm_status plan_create_core(int n_max, perm_dtype dtype, const perm_opts
     p->max_batch = o.max_batch ? o.max_batch : 65536;
     p->m_low = o.low_cols ? o.low_cols : 12;
     p->m_single = o.low_cols ? o.low_cols : 13;
+    if (shape.m_single >= 1 && shape.m_single <= kMaxLow && !o.low_cols) p->m_single = shape.m_single;
+    if (shape.layer_threads == 384 || shape.layer_threads == 512) p->layer_threads = shape.layer_threads;
+    if (shape.layer_grid_mult >= 1 && shape.layer_grid_mult <= 8) p->layer_grid_mult = shape.layer_grid_mult;
     // experiment knobs (results are bit-identical for every choice)
     if (const char* v = getenv("LIBPERM_SZ_LOW")) { int x = atoi(v); if (x >= 1 && x <= kMaxLow) p->m_low = x; }
-    if (const char* v = getenv("LIBPERM_SZ_THREADS")) { int x = atoi(v); if (sz_c128_threads_valid(x)) p->c128_threads = x; }
+    if (const char* v = getenv("LIBPERM_SZ_THREADS")) {
+        const int x = atoi(v);
+        if (sz_c128_threads_valid(x)) p->c128_threads = x;
+        if (sz_int_threads_valid(x)) p->int_threads = x;
+    }
+    if (const char* v = getenv("LIBPERM_SZ_TAIL_LAYERS")) p->tail_to_layers = atoi(v) != 0;
     if (shape.m_low >= 1 && shape.m_low <= kMaxLow) p->m_low = shape.m_low;
     if (dtype == PERM_C128 && sz_c128_threads_valid(shape.threads)) p->c128_threads = shape.threads;
     if (dtype != PERM_C128 && sz_int_threads_valid(shape.threads)) p->int_threads = shape.threads;
@@ -215,7 +230,7 @@ static perm_status plan_create_core(int n_max, perm_dtype dtype, const perm_opts
     size_t sz_batched = 0, sz_single = 0;
     const bool uses_sz = p->method == PERM_METHOD_SZ || (p->method == PERM_METHOD_AUTO && auto_uses_sz(dtype));
     if (uses_sz && n_max >= 1) {
-        p->sz_batch_nmax = sz_batch_limit(p);
+        p->sz_batch_nmax = sz_batch_limit(p, shape.batch_nmax >= 0 ? shape.batch_nmax : 20);
         // experiment knob: largest order of the one-CTA-per-matrix kernel (the others take the
         // layer path; both give the same bits)
         if (const char* v = getenv("LIBPERM_SZ_BATCH_NMAX")) {
@@ -320,9 +335,11 @@ int perm_plan_describe(perm_plan_t p, char* buf, size_t len) {
                     "{\"dtype\": \"%s\", \"n_max\": %d, \"method\": %d, \"flags\": %u, "
                     "\"sz_batch_nmax\": %d, \"sz_single_nmax\": %d, \"chain_width_batched\": %d, "
                     "\"chain_width_single\": %d, \"cta_threads\": %d, \"batched_grid\": %d, "
+                    "\"layer_cta_threads\": %d, \"layer_ctas_per_sm\": %d, "
                     "\"workspace_bytes\": %zu, \"out_words\": %d, \"autotuned\": %s}",
                     dt, p->n_max, p->method, p->flags, p->sz_batch_nmax, p->sz_single_nmax, p->m_low,
                     p->m_single, p->dtype == PERM_C128 ? p->c128_threads : p->int_threads, p->sz_grid,
+                    p->dtype == PERM_C128 ? p->layer_threads : 256, p->layer_grid_mult,
                     perm_plan_workspace_bytes(p), p->dtype == PERM_C128 ? 0 : p->out_words,
                     p->tuned ? "true" : "false");
 }
@@ -381,6 +398,15 @@ perm_status classify(perm_plan_t p, const int* sizes, int count, BatchLayout& L)
     }
     // longest matrices first for the persistent queue
     std::stable_sort(szb.begin(), szb.end(), [](const ItemDesc& a, const ItemDesc& b) { return a.n > b.n; });
+    // The persistent grid takes the matrices in rounds of one per CTA; a last, partial round
+    // would leave the other CTAs idle for a whole matrix's time.  Complex matrices of that round
+    // (the shortest, at the end of the queue) take the layer path instead, which spreads their
+    // chains over every SM after the batched launch.  Same bits either way.
+    if (!plain && p->dtype == PERM_C128 && p->tail_to_layers && (int)szb.size() > p->sz_grid) {
+        const size_t rem = szb.size() % (size_t)p->sz_grid;
+        for (size_t i = szb.size() - rem; i < szb.size(); i++) szs[szb[i].n].push_back(szb[i]);
+        szb.resize(szb.size() - rem);
+    }
     L.triv_at = L.desc.size();
     L.ntriv = triv.size();
     L.desc.insert(L.desc.end(), triv.begin(), triv.end());
@@ -430,7 +456,8 @@ perm_status enqueue(perm_plan_t p, const BatchLayout& L, const void* mats, const
         for (int b0 = 0; b0 < g.cnt; b0 += (int)per_launch) {
             const int c = (int)std::min<long long>(per_launch, g.cnt - b0);
             e = sz_launch_layers(p->dtype, mats, dd + g.at + b0, c, g.n, p->m_single, out, p->out_words,
-                                 item_status, p->ws, ws_item, 2 * p->num_sms, st);
+                                 item_status, p->ws, ws_item, p->layer_grid_mult * p->num_sms, st,
+                                 p->layer_threads);
             if (e != cudaSuccess) return PERM_ECUDA;
         }
     }
@@ -655,65 +682,81 @@ perm_status perm_ryser_finish(perm_plan_t p, int n, const void* partials, void* 
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
-// Autotuner (PERM_FLAG_AUTOTUNE).  Chooses the CTA size and the chain width of
-// the batched Store-zechin kernel by timing every candidate on a synthetic
-// batch of the plan's typical order; every candidate computes bit-identical
-// results (the summation order depends on neither), so tuning never changes a
-// result.  Choices are cached per (device, dtype, order) for the process, and
-// in the file named by LIBPERM_TUNE_CACHE when that is set.
+// Autotuner (PERM_FLAG_AUTOTUNE).  Times candidate launch shapes on synthetic
+// batches and keeps the fastest of each:
+//   1. the batched Store-zechin kernel: CTA size x chain width, at the plan's
+//      largest batched order (at most 20);
+//   2. complex plans with n_max >= 21: the largest order that still runs one
+//      CTA per matrix rather than the layer path (19..22), from batches of
+//      2 x SMs matrices per order;
+//   3. complex plans with n_max >= 21: the layer path's CTA size, chain width
+//      and CTAs per launch, on one matrix of order min(n_max, 24).
+// Every choice gives bit-identical results: every entry sums its terms over its
+// columns in ascending order whatever the shape.  Choices are cached per
+// (device, dtype, n_max) for the process, and in the file LIBPERM_TUNE_CACHE
+// names when that is set.
 // ---------------------------------------------------------------------------
 namespace {
 
-struct TuneChoice { int threads; int m_low; float ms; };
+struct TuneChoice {
+    PlanShape shape;
+    float ms = 0.f;      // the batched candidate's time (0: nothing tuned)
+};
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int>, TuneChoice> g_tune;
 
-bool tune_cache_lookup(int dev, int dtype, int n, TuneChoice* c) {
+bool tune_cache_lookup(int dev, int dtype, int n_max, TuneChoice* c) {
     std::lock_guard<std::mutex> g(g_tune_mu);
-    auto it = g_tune.find(std::make_tuple(dev, dtype, n));
+    auto it = g_tune.find(std::make_tuple(dev, dtype, n_max));
     if (it != g_tune.end()) { *c = it->second; return true; }
     const char* path = getenv("LIBPERM_TUNE_CACHE");
     if (!path) return false;
     FILE* f = fopen(path, "r");
     if (!f) return false;
     char name[256];
-    int fd, fn, th, m;
+    int fd, fn, th, m, bn, lt, ms_, lg;
     float ms;
     bool found = false;
-    while (fscanf(f, "%255s %d %d %d %d %f", name, &fd, &fn, &th, &m, &ms) == 6) {
-        if (strcmp(name, "perm-tune") == 0 && fd == dtype && fn == n) {
-            *c = TuneChoice{th, m, ms};
+    while (fscanf(f, "%255s %d %d %d %d %d %d %d %d %f", name, &fd, &fn, &th, &m, &bn, &lt, &ms_, &lg, &ms) == 10) {
+        if (strcmp(name, "perm-tune2") == 0 && fd == dtype && fn == n_max) {
+            c->shape.threads = th;
+            c->shape.m_low = m;
+            c->shape.batch_nmax = bn;
+            c->shape.layer_threads = lt;
+            c->shape.m_single = ms_;
+            c->shape.layer_grid_mult = lg;
+            c->ms = ms;
             found = true;
         }
     }
     fclose(f);
-    if (found) g_tune[std::make_tuple(dev, dtype, n)] = *c;
+    if (found) g_tune[std::make_tuple(dev, dtype, n_max)] = *c;
     return found;
 }
 
-void tune_cache_store(int dev, int dtype, int n, const TuneChoice& c) {
+void tune_cache_store(int dev, int dtype, int n_max, const TuneChoice& c) {
     std::lock_guard<std::mutex> g(g_tune_mu);
-    g_tune[std::make_tuple(dev, dtype, n)] = c;
+    g_tune[std::make_tuple(dev, dtype, n_max)] = c;
     if (const char* path = getenv("LIBPERM_TUNE_CACHE")) {
         if (FILE* f = fopen(path, "a")) {
-            fprintf(f, "perm-tune %d %d %d %d %.4f\n", dtype, n, c.threads, c.m_low, c.ms);
+            const PlanShape& s = c.shape;
+            fprintf(f, "perm-tune2 %d %d %d %d %d %d %d %d %.4f\n", dtype, n_max, s.threads, s.m_low,
+                    s.batch_nmax, s.layer_threads, s.m_single, s.layer_grid_mult, c.ms);
             fclose(f);
         }
     }
 }
 
-// Time one candidate on `count` synthetic matrices of order n (device buffers given).
-float time_candidate(int n, perm_dtype dtype, const perm_opts& base, int threads, int m,
-                     const void* d_mats, int count, void* d_out, cudaStream_t st) {
+// Time one plan shape on `count` synthetic matrices of order n (device buffers given):
+// the second of two calls, in milliseconds (-1 if the shape cannot run).
+float time_shape(int n, perm_dtype dtype, const perm_opts& base, const PlanShape& shape, int n_max,
+                 const void* d_mats, int count, void* d_out, cudaStream_t st) {
     perm_opts o = base;
     o.flags &= ~(PERM_FLAG_AUTOTUNE | PERM_FLAG_GRAPH | PERM_FLAG_PLAIN | PERM_FLAG_WIDE);
     o.max_batch = count;
     o.method = PERM_METHOD_SZ;
     perm_plan_t p = nullptr;
-    PlanShape shape;
-    shape.m_low = m;
-    shape.threads = threads;
-    if (plan_create_core(n, dtype, &o, nullptr, 0, shape, &p) != PERM_OK) return -1.f;
+    if (plan_create_core(n_max, dtype, &o, nullptr, 0, shape, &p) != PERM_OK) return -1.f;
     std::vector<int> sizes(count, n);
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
@@ -733,6 +776,26 @@ float time_candidate(int n, perm_dtype dtype, const perm_opts& base, int threads
     return ok ? ms : -1.f;
 }
 
+// Synthetic matrices for the tuner: a fixed LCG stream, complex entries of size
+// about 1/n, or 0/1 entries.
+std::vector<unsigned char> tune_matrices(perm_dtype dtype, int n, int count) {
+    const size_t eb = dtype == PERM_C128 ? 16 : 8;
+    std::vector<unsigned char> h((size_t)count * n * n * eb);
+    unsigned long long x = 0x9E3779B97F4A7C15ull;
+    for (size_t i = 0; i < (size_t)count * n * n; i++) {
+        x = x * 6364136223846793005ull + 1442695040888963407ull;
+        if (dtype == PERM_C128) {
+            double* d = reinterpret_cast<double*>(h.data()) + 2 * i;
+            d[0] = ((double)(x >> 11) * 0x1.0p-53 - 0.5) / n;
+            x = x * 6364136223846793005ull + 1442695040888963407ull;
+            d[1] = ((double)(x >> 11) * 0x1.0p-53 - 0.5) / n;
+        } else {
+            reinterpret_cast<long long*>(h.data())[i] = (long long)((x >> 33) & 1ull);
+        }
+    }
+    return h;
+}
+
 }  // namespace
 
 static perm_status plan_create_tuned(int n_max, perm_dtype dtype, const perm_opts* opts,
@@ -743,57 +806,70 @@ static perm_status plan_create_tuned(int n_max, perm_dtype dtype, const perm_opt
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return PERM_ECUDA;
-    // the order the batched kernel is tuned at: the plan's largest batched order, at most 20
-    const int n = std::min(n_max, 20);
-    TuneChoice best{0, 0, 0.f};
+    TuneChoice best;
     const bool uses_sz = o.method == PERM_METHOD_SZ || (o.method == PERM_METHOD_AUTO && auto_uses_sz(dtype));
-    if (uses_sz && n >= 14 && !o.low_cols && !o.ctas_per_sm &&
-        !tune_cache_lookup(dev, dtype, n, &best)) {
-        const int count = 4 * sms;
-        const size_t eb = dtype == PERM_C128 ? 16 : 8;
-        std::vector<unsigned char> h((size_t)count * n * n * eb);
-        unsigned long long x = 0x9E3779B97F4A7C15ull;   // fixed LCG stream
-        for (size_t i = 0; i < (size_t)count * n * n; i++) {
-            x = x * 6364136223846793005ull + 1442695040888963407ull;
-            if (dtype == PERM_C128) {
-                double* d = reinterpret_cast<double*>(h.data()) + 2 * i;
-                d[0] = ((double)(x >> 11) * 0x1.0p-53 - 0.5) / n;
-                x = x * 6364136223846793005ull + 1442695040888963407ull;
-                d[1] = ((double)(x >> 11) * 0x1.0p-53 - 0.5) / n;
-            } else {
-                reinterpret_cast<long long*>(h.data())[i] = (long long)((x >> 33) & 1ull);
-            }
-        }
+    const int n0 = std::min(n_max, 20);      // the order the batched kernel is tuned at
+    if (uses_sz && n0 >= 14 && !o.low_cols && !o.ctas_per_sm && !tune_cache_lookup(dev, dtype, n_max, &best)) {
+        const int nbig = std::min(std::max(n_max, n0), 24);
+        const int count = 2 * sms;
+        std::vector<unsigned char> h = tune_matrices(dtype, nbig, count);
         void *dm = nullptr, *dout = nullptr;
         cudaStream_t st = nullptr;
-        bool ok = cudaMalloc(&dm, h.size()) == cudaSuccess && cudaMalloc(&dout, (size_t)count * 16) == cudaSuccess &&
+        bool ok = cudaMalloc(&dm, h.size()) == cudaSuccess && cudaMalloc(&dout, (size_t)count * 32) == cudaSuccess &&
                   cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess &&
                   cudaMemcpy(dm, h.data(), h.size(), cudaMemcpyHostToDevice) == cudaSuccess;
-        if (ok) {
-            const int thr_c[3] = {256, 384, 512};
-            const int thr_i[2] = {256, 512};
-            const int* thr = dtype == PERM_C128 ? thr_c : thr_i;
-            const int nthr = dtype == PERM_C128 ? 3 : 2;
-            for (int ti = 0; ti < nthr; ti++)
-                for (int m = 11; m <= 13; m++) {
-                    const float ms = time_candidate(n, dtype, o, thr[ti], m, dm, count, dout, st);
-                    if (ms > 0.f && (best.ms == 0.f || ms < best.ms)) best = TuneChoice{thr[ti], m, ms};
+        // (1) batched kernel: CTA size x chain width (the matrices of order n0 are the first
+        // n0 x n0 elements of each synthetic block, read as concatenated matrices)
+        const int thr_c[3] = {256, 384, 512};
+        const int thr_i[2] = {256, 512};
+        const int* thr = dtype == PERM_C128 ? thr_c : thr_i;
+        const int nthr = dtype == PERM_C128 ? 3 : 2;
+        for (int ti = 0; ok && ti < nthr; ti++)
+            for (int m = 11; m <= 13; m++) {
+                PlanShape sh;
+                sh.threads = thr[ti];
+                sh.m_low = m;
+                const float ms = time_shape(n0, dtype, o, sh, n0, dm, count, dout, st);
+                if (ms > 0.f && (best.ms == 0.f || ms < best.ms)) { best.shape = sh; best.ms = ms; }
+            }
+        if (ok && best.ms > 0.f && dtype == PERM_C128 && n_max >= 21) {
+            // (2) the batched / layer crossover, order by order while the batched kernel wins
+            int cross = 18;
+            for (int n = 19; n <= std::min(n_max, 22); n++) {
+                PlanShape b = best.shape, l = best.shape;
+                b.batch_nmax = 22;
+                l.batch_nmax = 0;
+                const float tb = time_shape(n, dtype, o, b, n, dm, count, dout, st);
+                const float tl = time_shape(n, dtype, o, l, n, dm, count, dout, st);
+                if (tb > 0.f && (tl <= 0.f || tb <= tl)) cross = n;
+                else break;
+            }
+            best.shape.batch_nmax = cross;
+            // (3) the layer path on one matrix of order nbig
+            const int cand[6][3] = {{512, 13, 1}, {512, 13, 2}, {384, 12, 2}, {384, 12, 4}, {512, 12, 1}, {512, 12, 2}};
+            float lbest = 0.f;
+            for (const auto& c : cand) {
+                PlanShape sh = best.shape;
+                sh.layer_threads = c[0];
+                sh.m_single = c[1];
+                sh.layer_grid_mult = c[2];
+                const float ms = time_shape(nbig, dtype, o, sh, nbig, dm, 1, dout, st);
+                if (ms > 0.f && (lbest == 0.f || ms < lbest)) {
+                    lbest = ms;
+                    best.shape.layer_threads = c[0];
+                    best.shape.m_single = c[1];
+                    best.shape.layer_grid_mult = c[2];
                 }
+            }
         }
         if (st) cudaStreamDestroy(st);
         if (dm) cudaFree(dm);
         if (dout) cudaFree(dout);
         cudaGetLastError();
-        if (best.ms > 0.f) tune_cache_store(dev, dtype, n, best);
+        if (best.ms > 0.f) tune_cache_store(dev, dtype, n_max, best);
     }
-    // the tuned chain width applies to the batched path; the one-matrix path keeps its own
     perm_plan_t p = nullptr;
-    PlanShape shape;
-    if (best.ms > 0.f) {
-        shape.m_low = best.m_low;
-        shape.threads = best.threads;
-    }
-    perm_status s = plan_create_core(n_max, dtype, &o, nullptr, 0, shape, &p);
+    perm_status s = plan_create_core(n_max, dtype, &o, nullptr, 0, best.ms > 0.f ? best.shape : PlanShape{}, &p);
     if (s != PERM_OK) return s;
     if (p) p->tuned = best.ms > 0.f;
     *out = p;

@@ -234,9 +234,11 @@ cudaError_t sz_launch_single(int dtype, const void* mats, long long offset, int 
 // in each layer launch; matrix c of the list uses the workspace slice
 // [c * ws_bytes_per_item, (c + 1) * ws_bytes_per_item), ws_bytes_per_item >=
 // sz_matrix_workspace_bytes(dtype, n, m).
+// threads: CTA size of the complex layer kernel, 384 (two CTAs per SM) or 512 (one; also
+// for 0); every choice gives the same bits.
 cudaError_t sz_launch_layers(int dtype, const void* mats, const ItemDesc* items, int count, int n, int m,
                              void* out, int out_words, int* item_status, void* workspace,
-                             size_t ws_bytes_per_item, int grid_cap, cudaStream_t st);
+                             size_t ws_bytes_per_item, int grid_cap, cudaStream_t st, int threads = 0);
 
 // Ryser: every matrix's codes are cut into ryser_parts(dtype, n) CTA-sized
 // pieces (a function of n only).  One launch per distinct order n.  allow192:

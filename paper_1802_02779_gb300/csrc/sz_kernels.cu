@@ -62,7 +62,7 @@ namespace perm {
 namespace {
 
 constexpr int kBinomDim = 24;            // C(x, y) for x < 24 (t <= 21, m <= 13)
-constexpr int kThreadsC128Single = 512;   // one matrix over the whole GPU: one CTA per SM
+constexpr int kThreadsC128Single = 512;   // layer path, default: one CTA per SM (384: two)
 constexpr int kThreadsInt = 256;          // integers: up to four CTAs per SM
 constexpr int kMaskTableLen = (2 << kMaxLow) - 2;   // sum_{m=1..13} 2^m
 
@@ -590,7 +590,8 @@ sz_batched_int(const long long* __restrict__ mats, const ItemDesc* __restrict__ 
 // Each chain is computed exactly as in the batched kernels, so results do not
 // depend on how many matrices share a launch.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreadsC128Single, 1)
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS, THREADS <= 384 ? 2 : 1)
 sz_layer_c128(const double2* __restrict__ mats, const ItemDesc* __restrict__ items, ItemDesc single,
               int count, int n, int m_param, int s, double2* out, int* item_status,
               unsigned long long* workspace, size_t ws_words_per_item) {
@@ -861,13 +862,14 @@ namespace {
 // matrix `single` when items == nullptr).
 cudaError_t sz_launch_layers_impl(int dtype, const void* mats, const ItemDesc* items, ItemDesc single,
                                   int count, int n, int m, void* out, int out_words, int* item_status,
-                                  void* workspace, size_t ws_bytes_per_item, int grid_cap,
+                                  void* workspace, size_t ws_bytes_per_item, int grid_cap, int threads,
                                   cudaStream_t st) {
     if (count <= 0) return cudaSuccess;
     const int mm = sz_low_for(n, m);
     const int t = n - mm;
     const int smem = sz_smem_bytes(dtype, n, m);
-    const void* fn = dtype == PERM_C128 ? (const void*)sz_layer_c128
+    const bool c384 = threads == 384;
+    const void* fn = dtype == PERM_C128 ? (c384 ? (const void*)sz_layer_c128<384> : (const void*)sz_layer_c128<512>)
                    : (dtype == PERM_U01 ? (const void*)sz_layer_int<true> : (const void*)sz_layer_int<false>);
     cudaError_t e = set_smem(fn, smem);
     if (e != cudaSuccess) return e;
@@ -875,8 +877,12 @@ cudaError_t sz_launch_layers_impl(int dtype, const void* mats, const ItemDesc* i
     for (int s = 0; s <= t; s++) {
         const unsigned long long tasks = binom_calc(t, s) * (unsigned long long)count;
         const int grid = (int)std::min<unsigned long long>(tasks, (unsigned long long)grid_cap);
-        if (dtype == PERM_C128) {
-            sz_layer_c128<<<grid, kThreadsC128Single, smem, st>>>(
+        if (dtype == PERM_C128 && c384) {
+            sz_layer_c128<384><<<grid, 384, smem, st>>>(
+                (const double2*)mats, items, single, count, n, m, s, (double2*)out, item_status,
+                (unsigned long long*)workspace, wpi);
+        } else if (dtype == PERM_C128) {
+            sz_layer_c128<kThreadsC128Single><<<grid, kThreadsC128Single, smem, st>>>(
                 (const double2*)mats, items, single, count, n, m, s, (double2*)out, item_status,
                 (unsigned long long*)workspace, wpi);
         } else if (dtype == PERM_U01) {
@@ -898,16 +904,16 @@ cudaError_t sz_launch_layers_impl(int dtype, const void* mats, const ItemDesc* i
 
 cudaError_t sz_launch_layers(int dtype, const void* mats, const ItemDesc* items, int count, int n, int m,
                              void* out, int out_words, int* item_status, void* workspace,
-                             size_t ws_bytes_per_item, int grid_cap, cudaStream_t st) {
+                             size_t ws_bytes_per_item, int grid_cap, cudaStream_t st, int threads) {
     return sz_launch_layers_impl(dtype, mats, items, ItemDesc{0, n, 0}, count, n, m, out, out_words,
-                                 item_status, workspace, ws_bytes_per_item, grid_cap, st);
+                                 item_status, workspace, ws_bytes_per_item, grid_cap, threads, st);
 }
 
 cudaError_t sz_launch_single(int dtype, const void* mats, long long offset, int n, int m,
                              int out_index, void* out, int out_words, int* item_status,
                              void* workspace, int grid_cap, cudaStream_t st) {
     return sz_launch_layers_impl(dtype, mats, nullptr, ItemDesc{offset, n, out_index}, 1, n, m, out,
-                                 out_words, item_status, workspace, 0, grid_cap, st);
+                                 out_words, item_status, workspace, 0, grid_cap, 0, st);
 }
 
 cudaError_t sz_preload(int dtype) {
@@ -919,7 +925,8 @@ cudaError_t sz_preload(int dtype) {
         fns[k++] = c128_batched_fn(256);
         fns[k++] = c128_batched_fn(384);
         fns[k++] = c128_batched_fn(512);
-        fns[k++] = (const void*)sz_layer_c128;
+        fns[k++] = (const void*)sz_layer_c128<384>;
+        fns[k++] = (const void*)sz_layer_c128<kThreadsC128Single>;
     } else {
         for (int n_max : {20, 34})
             for (int threads : {256, 512}) fns[k++] = (const void*)pick_int_batched(dtype, n_max, threads);

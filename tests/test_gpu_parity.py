@@ -229,6 +229,30 @@ def test_autotuned_plan_same_bits(lp, dtype):
         assert tuned == plain
 
 
+def test_autotuned_crossover_and_layer_shape_same_bits(lp, tmp_path, monkeypatch):
+    """A complex plan of n_max = 24 tunes the batched kernel, the batched/layer
+    crossover (19..22) and the layer path's CTA size, chain width and grid; every
+    tuned choice is reported by perm_plan_describe, kept in LIBPERM_TUNE_CACHE, and
+    gives the default plan's bits on a batch that takes both paths."""
+    monkeypatch.setenv("LIBPERM_TUNE_CACHE", str(tmp_path / "tune.txt"))
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    ns = [16, 19, 20, 21, 22, 24] * ((sms + 5) // 6 + 1)
+    mats = [rand_complex(n, 9500 + i) for i, n in enumerate(ns)]
+    with lp.Plan(24, "c128", flags=lp.FLAG_AUTOTUNE, max_batch=len(mats)) as pt:
+        d = pt.describe()
+        assert d["autotuned"] is True
+        assert 18 <= d["sz_batch_nmax"] <= 22
+        assert (d["layer_cta_threads"], d["chain_width_single"]) in ((512, 13), (384, 12), (512, 12))
+        assert d["layer_ctas_per_sm"] in (1, 2, 4)
+        tuned = lp.permanents(mats, "c128", plan=pt)
+    assert "perm-tune2" in (tmp_path / "tune.txt").read_text()
+    with lp.Plan(24, "c128", max_batch=len(mats)) as p0:
+        plain = lp.permanents(mats, "c128", plan=p0)
+    assert list(tuned) == list(plain)
+    for i in (0, 3, 5):
+        assert abs(tuned[i] - oracle_c(mats[i])) <= tol_c(mats[i])
+
+
 # ---------------------------------------------------------------------------
 # all collision-free patterns in one pass (perm_patterns)
 # ---------------------------------------------------------------------------
