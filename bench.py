@@ -117,10 +117,10 @@ class Clocks:
 
 
 # DRAM bytes (read + write) per n = 20 complex matrix of sz_batched_c128, from the ncu capture
-# summarised in profiles/sz_batched_c128_n20.md (304 matrices: 29.754227 GB + 7.624871 GB).
+# summarised in profiles/sz_batched_c128_n20.md (304 matrices: 29.750551 GB + 7.623576 GB).
 # Valid only for the kernel source it was measured on; otherwise the bench reports null.
-TRAFFIC_C128_PER_MATRIX = (29.754227e9 + 7.624871e9) / 304
-TRAFFIC_SOURCE_SHA256 = "b8ab79e02bc096d0744d08e057785e206a6c695a7ceb85b83844dcf1e8fe1413"
+TRAFFIC_C128_PER_MATRIX = (29.750551e9 + 7.623576e9) / 304
+TRAFFIC_SOURCE_SHA256 = "7dd7e272a530ec5e99e854805fad8a8172d653487622195d8ece34b9941bff6e"
 
 
 def traffic_per_launch(count: int):
@@ -317,6 +317,13 @@ def run_gpu(args, rank, world):
         return
 
     c_kernel_ms = float(np.mean(c_ms))
+    # launches per step: the batched complex kernel, the layer launches (t + 1 of them) of its
+    # last partial round when the batch is not a whole number of rounds, then the 0/1 half
+    # (Ryser: width, Gray-code and finishing kernels; --int-method sz: one batched kernel)
+    dc = pc.describe()
+    tail = count % dc["batched_grid"] if count > dc["batched_grid"] else 0
+    launches_per_step = 1 + ((N - dc["chain_width_single"] + 1) if tail else 0) + \
+        (1 if args.int_method == "sz" else 3)
     # achieved: the method's own work per permanent (n(2^(n-1)-1) complex multiplications at
     # 6 flops, (n-2)2^(n-1)+1 complex additions at 2), the per-unit figure of the roofline
     flops = sz_c128_standard_flops(N) * count
@@ -359,10 +366,7 @@ def run_gpu(args, rank, world):
             "complex_perm_per_s": count / (c_kernel_ms / 1000.0),
             "zero_one_perm_per_s": count / (float(np.mean(i_ms)) / 1000.0),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            # per step: the batched Store-zechin kernel (complex) and the Ryser width, Gray-code
-            # and finishing kernels (0/1, all matrices in one group), or one batched
-            # Store-zechin integer kernel with --int-method sz
-            "gpu_launches": (2 if args.int_method == "sz" else 4) * args.steps, "clocks": ck}
+            "gpu_launches": launches_per_step * args.steps, "clocks": ck}
     line.update(extras)
     print(json.dumps(line), flush=True)
     if dist:
@@ -570,6 +574,10 @@ def measure_uneven(lp, torch, stream, count=20000):
             p.close()
     res["batched_vs_plain"] = res["batched_perm_per_s"] / res["plain_perm_per_s"]
     res["graph_vs_plain"] = res["graph_perm_per_s"] / res["plain_perm_per_s"]
+    # the complex requests' Store-zechin work (the method's count, as the roofline) per second
+    work = sum(sz_c128_standard_flops(r.n) for r in reqs if r.dtype == "c128")
+    for name in ("plain", "batched", "graph"):
+        res[name + "_complex_tflops"] = work * res[name + "_perm_per_s"] / count / 1e12
     res["same_bits"] = all((results["plain"][dt] == results[k][dt]).all()
                            for k in ("batched", "graph") for dt in groups)
     return res
