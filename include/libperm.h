@@ -112,7 +112,8 @@ typedef enum perm_method {
                                  batches and keep the fastest: the batched Store-zechin kernel's
                                  CTA size and chain width; for complex plans of n_max >= 21 also
                                  the largest order run one CTA per matrix (19..22) and the layer
-                                 path's CTA size, chain width and CTAs per launch.  Results are
+                                 path's CTA size, chain width and CTAs per launch for orders up
+                                 to 24.  Results are
                                  bit-identical for every choice; perm_plan_describe reports
                                  them; cached per (device, dtype, n_max) for the process and in
                                  the file LIBPERM_TUNE_CACHE names, if set */

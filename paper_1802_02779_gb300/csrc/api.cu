@@ -58,9 +58,14 @@ struct perm_plan_s {
     int max_batch = 65536;
     int num_sms = 0;
     int m_low = 12;               // chain width of the batched kernel (two CTAs per SM)
-    int m_single = 13;            // chain width of the one-matrix-over-the-GPU path
-    int layer_threads = 512;      // CTA size of that path's complex kernel (384: two CTAs per SM)
-    int layer_grid_mult = 2;      // its CTAs per launch, in units of the SM count
+    // layer path (matrices over the whole GPU, one launch per layer): orders above
+    // kLayerSmallN, and (the *_small fields) orders up to it
+    int m_single = 13;            // chain width
+    int layer_threads = 512;      // CTA size of the complex kernel (384: two CTAs per SM)
+    int layer_grid_mult = 1;      // CTAs per launch, in units of the SM count
+    int m_small = 12;
+    int layer_threads_small = 384;
+    int layer_grid_small = 2;
     bool tail_to_layers = true;   // the batched kernel's last partial round takes the layer path
     int c128_threads = 384;       // CTA size of the batched complex kernel
     int int_threads = 256;        // CTA size of the batched integer kernel
@@ -131,6 +136,9 @@ int sz_batch_limit(perm_plan_t p, int complex_cap = 20) {
     return best;
 }
 
+// Chain width of the layer path for order n.
+int layer_m(perm_plan_t p, int n) { return n <= kLayerSmallN ? p->m_small : p->m_single; }
+
 }  // namespace
 
 // Plan creation with an optional caller-owned Store-zechin workspace.
@@ -143,9 +151,9 @@ struct PlanShape {
     int m_low = 0;           // chain width of the batched kernel
     int threads = 0;         // CTA size of the batched kernel
     int batch_nmax = -1;     // largest complex order of the batched kernel (-1: 20)
-    int layer_threads = 0;   // CTA size of the layer path's complex kernel (384 or 512)
-    int m_single = 0;        // chain width of the layer path
-    int layer_grid_mult = 0; // CTAs per layer launch in units of the SM count
+    int layer_threads = 0;   // layer path, complex orders <= kLayerSmallN: CTA size (384 or 512),
+    int m_single = 0;        // chain width,
+    int layer_grid_mult = 0; // and CTAs per layer launch in units of the SM count
 };
 static perm_status plan_create_core(int n_max, perm_dtype dtype, const perm_opts* opts, void* ext_ws,
                                     size_t ext_ws_bytes, PlanShape shape, perm_plan_t* out);
@@ -203,10 +211,13 @@ static perm_status plan_create_core(int n_max, perm_dtype dtype, const perm_opts
     p->out_words = (o.flags & PERM_FLAG_WIDE) ? 4 : 2;
     p->max_batch = o.max_batch ? o.max_batch : 65536;
     p->m_low = o.low_cols ? o.low_cols : 12;
-    p->m_single = o.low_cols ? o.low_cols : 13;
-    if (shape.m_single >= 1 && shape.m_single <= kMaxLow && !o.low_cols) p->m_single = shape.m_single;
-    if (shape.layer_threads == 384 || shape.layer_threads == 512) p->layer_threads = shape.layer_threads;
-    if (shape.layer_grid_mult >= 1 && shape.layer_grid_mult <= 8) p->layer_grid_mult = shape.layer_grid_mult;
+    sz_layer_default_shape(kLayerSmallN + 1, &p->m_single, &p->layer_threads);
+    sz_layer_default_shape(kLayerSmallN, &p->m_small, &p->layer_threads_small);
+    if (dtype != PERM_C128) p->m_small = p->m_single;   // integers: one shape (the 256-thread kernel)
+    if (o.low_cols) p->m_single = p->m_small = o.low_cols;
+    if (shape.m_single >= 1 && shape.m_single <= kMaxLow && !o.low_cols) p->m_small = shape.m_single;
+    if (shape.layer_threads == 384 || shape.layer_threads == 512) p->layer_threads_small = shape.layer_threads;
+    if (shape.layer_grid_mult >= 1 && shape.layer_grid_mult <= 8) p->layer_grid_small = shape.layer_grid_mult;
     // experiment knobs (results are bit-identical for every choice)
     if (const char* v = getenv("LIBPERM_SZ_LOW")) { int x = atoi(v); if (x >= 1 && x <= kMaxLow) p->m_low = x; }
     if (const char* v = getenv("LIBPERM_SZ_THREADS")) {
@@ -215,6 +226,14 @@ static perm_status plan_create_core(int n_max, perm_dtype dtype, const perm_opts
         if (sz_int_threads_valid(x)) p->int_threads = x;
     }
     if (const char* v = getenv("LIBPERM_SZ_TAIL_LAYERS")) p->tail_to_layers = atoi(v) != 0;
+    if (const char* v = getenv("LIBPERM_SZ_LAYER_THREADS")) {
+        const int x = atoi(v);
+        if (x == 384 || x == 512) p->layer_threads = p->layer_threads_small = x;
+    }
+    if (const char* v = getenv("LIBPERM_SZ_LAYER_GRID")) {
+        const int x = atoi(v);
+        if (x >= 1 && x <= 8) p->layer_grid_mult = p->layer_grid_small = x;
+    }
     if (shape.m_low >= 1 && shape.m_low <= kMaxLow) p->m_low = shape.m_low;
     if (dtype == PERM_C128 && sz_c128_threads_valid(shape.threads)) p->c128_threads = shape.threads;
     if (dtype != PERM_C128 && sz_int_threads_valid(shape.threads)) p->int_threads = shape.threads;
@@ -246,11 +265,12 @@ static perm_status plan_create_core(int n_max, perm_dtype dtype, const perm_opts
         sz_batched = p->sz_ws_per_cta * (size_t)p->sz_grid;
         // largest n whose single-matrix workspace fits the remaining budget
         for (int n = 1; n <= std::min(n_max, kMaxNSZ); n++) {
-            const size_t need = sz_matrix_workspace_bytes(dtype, n, p->m_single);
-            if (need + (size_t)(1 << 20) <= p->budget) p->sz_single_nmax = n;
+            const size_t need = sz_matrix_workspace_bytes(dtype, n, layer_m(p, n));
+            if (need + (size_t)(1 << 20) <= p->budget) {
+                p->sz_single_nmax = n;
+                sz_single = std::max(sz_single, need);
+            }
         }
-        if (p->sz_single_nmax > 0)
-            sz_single = sz_matrix_workspace_bytes(dtype, p->sz_single_nmax, p->m_single);
         if (sz_batched > p->budget) {   // shrink the persistent grid to the budget
             p->sz_grid = (int)std::max<size_t>(1, p->budget / std::max<size_t>(1, p->sz_ws_per_cta));
             sz_batched = p->sz_ws_per_cta * (size_t)p->sz_grid;
@@ -335,11 +355,14 @@ int perm_plan_describe(perm_plan_t p, char* buf, size_t len) {
                     "{\"dtype\": \"%s\", \"n_max\": %d, \"method\": %d, \"flags\": %u, "
                     "\"sz_batch_nmax\": %d, \"sz_single_nmax\": %d, \"chain_width_batched\": %d, "
                     "\"chain_width_single\": %d, \"cta_threads\": %d, \"batched_grid\": %d, "
-                    "\"layer_cta_threads\": %d, \"layer_ctas_per_sm\": %d, "
+                    "\"layer_cta_threads\": %d, \"layer_ctas_per_sm\": %d, \"layer_small_nmax\": %d, "
+                    "\"chain_width_layer_small\": %d, \"layer_cta_threads_small\": %d, "
+                    "\"layer_ctas_per_sm_small\": %d, "
                     "\"workspace_bytes\": %zu, \"out_words\": %d, \"autotuned\": %s}",
                     dt, p->n_max, p->method, p->flags, p->sz_batch_nmax, p->sz_single_nmax, p->m_low,
                     p->m_single, p->dtype == PERM_C128 ? p->c128_threads : p->int_threads, p->sz_grid,
-                    p->dtype == PERM_C128 ? p->layer_threads : 256, p->layer_grid_mult,
+                    p->dtype == PERM_C128 ? p->layer_threads : 256, p->layer_grid_mult, kLayerSmallN,
+                    p->m_small, p->dtype == PERM_C128 ? p->layer_threads_small : 256, p->layer_grid_small,
                     perm_plan_workspace_bytes(p), p->dtype == PERM_C128 ? 0 : p->out_words,
                     p->tuned ? "true" : "false");
 }
@@ -449,15 +472,17 @@ perm_status enqueue(perm_plan_t p, const BatchLayout& L, const void* mats, const
         // most of the GPU idle, several fill it.  Two CTAs' worth of chains per SM and
         // layer amortise the per-CTA set-up, and every layer is its own launch, which gives
         // the scheduler a point to interleave work from higher-priority streams.
-        const size_t ws_item = sz_matrix_workspace_bytes(p->dtype, g.n, p->m_single);
+        const int lm = layer_m(p, g.n);
+        const bool small = g.n <= kLayerSmallN;
+        const size_t ws_item = sz_matrix_workspace_bytes(p->dtype, g.n, lm);
         long long per_launch = ws_item ? (long long)(p->ws_bytes / ws_item) : (long long)g.cnt;
         per_launch = std::max<long long>(1, per_launch);
         if (plain) per_launch = 1;
         for (int b0 = 0; b0 < g.cnt; b0 += (int)per_launch) {
             const int c = (int)std::min<long long>(per_launch, g.cnt - b0);
-            e = sz_launch_layers(p->dtype, mats, dd + g.at + b0, c, g.n, p->m_single, out, p->out_words,
-                                 item_status, p->ws, ws_item, p->layer_grid_mult * p->num_sms, st,
-                                 p->layer_threads);
+            e = sz_launch_layers(p->dtype, mats, dd + g.at + b0, c, g.n, lm, out, p->out_words, item_status,
+                                 p->ws, ws_item, (small ? p->layer_grid_small : p->layer_grid_mult) * p->num_sms,
+                                 st, small ? p->layer_threads_small : p->layer_threads);
             if (e != cudaSuccess) return PERM_ECUDA;
         }
     }
@@ -690,7 +715,9 @@ perm_status perm_ryser_finish(perm_plan_t p, int n, const void* partials, void* 
 //      CTA per matrix rather than the layer path (19..22), from batches of
 //      2 x SMs matrices per order;
 //   3. complex plans with n_max >= 21: the layer path's CTA size, chain width
-//      and CTAs per launch, on one matrix of order min(n_max, 24).
+//      and CTAs per launch for orders up to 24, on one matrix of order
+//      min(n_max, 24) (larger orders keep chains of 2^13 at one 512-thread CTA
+//      per SM, measured faster at every order from 25 to 32).
 // Every choice gives bit-identical results: every entry sums its terms over its
 // columns in ascending order whatever the shape.  Choices are cached per
 // (device, dtype, n_max) for the process, and in the file LIBPERM_TUNE_CACHE
@@ -845,8 +872,8 @@ static perm_status plan_create_tuned(int n_max, perm_dtype dtype, const perm_opt
                 else break;
             }
             best.shape.batch_nmax = cross;
-            // (3) the layer path on one matrix of order nbig
-            const int cand[6][3] = {{512, 13, 1}, {512, 13, 2}, {384, 12, 2}, {384, 12, 4}, {512, 12, 1}, {512, 12, 2}};
+            // (3) the layer path's shape for orders up to kLayerSmallN, on one matrix of order nbig
+            const int cand[4][3] = {{384, 12, 2}, {384, 12, 4}, {512, 13, 1}, {512, 12, 2}};
             float lbest = 0.f;
             for (const auto& c : cand) {
                 PlanShape sh = best.shape;

@@ -236,6 +236,17 @@ cudaError_t sz_launch_single(int dtype, const void* mats, long long offset, int 
 // sz_matrix_workspace_bytes(dtype, n, m).
 // threads: CTA size of the complex layer kernel, 384 (two CTAs per SM) or 512 (one; also
 // for 0); every choice gives the same bits.
+//
+// Default shape of the complex layer path by order (measured on GB300, one matrix alone):
+// up to order 24 chains of 2^12 entries at two 384-thread CTAs per SM (more, smaller chains fill
+// the small first and last layers: n = 24 2.08 ms against 2.56 ms), above it chains of 2^13 at
+// one 512-thread CTA per SM (one outer column fewer, so fewer predecessor loads: n = 28 25.9 ms
+// against 32.3 ms, n = 32 454 ms against 572 ms).
+constexpr int kLayerSmallN = 24;
+inline void sz_layer_default_shape(int n, int* m, int* threads) {
+    *m = n <= kLayerSmallN ? 12 : 13;
+    *threads = n <= kLayerSmallN ? 384 : 512;
+}
 cudaError_t sz_launch_layers(int dtype, const void* mats, const ItemDesc* items, int count, int n, int m,
                              void* out, int out_words, int* item_status, void* workspace,
                              size_t ws_bytes_per_item, int grid_cap, cudaStream_t st, int threads = 0);

@@ -16,8 +16,8 @@
 //               at the head of the queue plus the queued requests of the same
 //               order behind it (they share every layer launch).  A job is
 //               admitted while the tables of all jobs in flight stay within
-//               the budget -- C(t, t/2) chains of 2^13 entries, two layers,
-//               per matrix -- and its tables come from a stream-ordered memory
+//               the budget -- C(t, t/2) chains of 2^12 or 2^13 entries, two
+//               layers, per matrix -- and its tables come from a stream-ordered memory
 //               pool and return to it when the job's kernels finish, so the
 //               next job is admitted as memory frees up.  Middle priority.
 //   Ryser lane  every other order (Ryser's formula, Section 3.3, which needs no
@@ -59,7 +59,6 @@ constexpr int kQueueCap = 1 << 16;
 constexpr int kFastBatch = 4096;
 constexpr int kTableSlots = 4;           // table-lane jobs in flight at once
 constexpr int kTableJob = 16;            // requests of one order per table job
-constexpr int kTableLow = 13;            // chain width of the one-matrix Store-zechin path
 constexpr int kRyserBatch = 64;
 constexpr double kRyserBatchCodes = 34359738368.0;   // 2^35 Gray codes per Ryser batch (>= 1 request)
 constexpr size_t kResultSlot = 32;       // bytes reserved per result in the slot buffers
@@ -211,7 +210,14 @@ perm_plan_t lane_plan(perm_server_t s, Lane& L, int dtype) {
 }
 
 // Table bytes of one complex matrix of order n on the table lane.
-size_t table_bytes(int n) { return sz_matrix_workspace_bytes(PERM_C128, n, kTableLow); }
+// Table bytes of one complex matrix of order n on the table lane (the layer path's default
+// shape for that order).
+int table_low(int n) {
+    int m = 0, threads = 0;
+    sz_layer_default_shape(n, &m, &threads);
+    return m;
+}
+size_t table_bytes(int n) { return sz_matrix_workspace_bytes(PERM_C128, n, table_low(n)); }
 
 // Gray codes Ryser walks for one request (the Ryser lane's batch bound).
 double ryser_codes(const Request* r) {
@@ -300,9 +306,11 @@ int table_launch(perm_server_t s, Slot& S, std::vector<Request*>& job) {
     bool ok = cudaMemcpyAsync(S.d_in, S.h_in, off, cudaMemcpyHostToDevice, S.stream) == cudaSuccess &&
               cudaMemcpyAsync(S.d_desc, S.h_desc, (size_t)c * sizeof(ItemDesc), cudaMemcpyHostToDevice,
                               S.stream) == cudaSuccess;
+    int lm = 0, lthreads = 0;
+    sz_layer_default_shape(n, &lm, &lthreads);
     if (ok)
-        ok = sz_launch_layers(PERM_C128, S.d_in, S.d_desc, c, n, kTableLow, S.d_out, 2, S.d_status, ws, ws_item,
-                              2 * s->num_sms, S.stream) == cudaSuccess;
+        ok = sz_launch_layers(PERM_C128, S.d_in, S.d_desc, c, n, lm, S.d_out, 2, S.d_status, ws, ws_item,
+                              (lthreads == 384 ? 2 : 1) * s->num_sms, S.stream, lthreads) == cudaSuccess;
     if (cudaFreeAsync(ws, S.stream) != cudaSuccess) ok = false;
     if (ok) ok = slot_finish_launch(S, (size_t)c * 16, c);
     if (!ok) return -1;
