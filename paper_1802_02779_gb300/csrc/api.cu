@@ -250,16 +250,20 @@ static perm_status plan_create_core(int n_max, perm_dtype dtype, const perm_opts
     const bool uses_sz = p->method == PERM_METHOD_SZ || (p->method == PERM_METHOD_AUTO && auto_uses_sz(dtype));
     if (uses_sz && n_max >= 1) {
         p->sz_batch_nmax = sz_batch_limit(p, shape.batch_nmax >= 0 ? shape.batch_nmax : 20);
+        // The workspace is sized for the batched kernel at its default largest order (or the tuned
+        // one, if larger) even when a smaller order is chosen: the layer path then shares the same
+        // workspace among the matrices of one order, as many as it holds.
+        const int ws_nmax = std::max(p->sz_batch_nmax, sz_batch_limit(p, 20));
         // experiment knob: largest order of the one-CTA-per-matrix kernel (the others take the
         // layer path; both give the same bits)
         if (const char* v = getenv("LIBPERM_SZ_BATCH_NMAX")) {
             const int x = atoi(v);
             if (x >= 0 && x < p->sz_batch_nmax) p->sz_batch_nmax = x;
         }
-        p->sz_ws_per_cta = sz_matrix_workspace_bytes(dtype, p->sz_batch_nmax, p->m_low);
+        p->sz_ws_per_cta = sz_matrix_workspace_bytes(dtype, ws_nmax, p->m_low);
         if (sz_init_tables() != cudaSuccess) { delete p; return PERM_ECUDA; }
         int per_sm = o.ctas_per_sm ? o.ctas_per_sm
-                                   : sz_batched_occupancy(dtype, std::max(1, p->sz_batch_nmax), p->m_low,
+                                   : sz_batched_occupancy(dtype, std::max(1, ws_nmax), p->m_low,
                                                           dtype == PERM_C128 ? p->c128_threads : p->int_threads);
         p->sz_grid = p->num_sms * per_sm;
         sz_batched = p->sz_ws_per_cta * (size_t)p->sz_grid;
