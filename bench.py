@@ -411,9 +411,10 @@ def measure_extras(lp, torch, cm, im, stream, c_kernel_ms, count):
             torch.cuda.synchronize()
             res[name + "_ms"] = e0.elapsed_time(e1)
             res[name + "_value"] = [float(o32[0].real), float(o32[0].imag)]
-    res["sz_fp64_tflops"] = sz_c128_flops(32) / (res["store_zechin_ms"] / 1000.0) / 1e12
+    res["sz_work_tflops"] = sz_c128_standard_flops(32) / (res["store_zechin_ms"] / 1000.0) / 1e12
     out["n32"] = res
     out["n34"] = measure_n34(lp, torch, stream)
+    out["n35"] = measure_n34(lp, torch, stream, n=35, budget_gb=200)
     out["integer_methods"] = measure_integer_methods(lp, torch, im, stream, count)
     out["wide"] = measure_wide(lp, torch, stream)
     out["five_boson"] = measure_five_boson(lp, torch, stream)
@@ -432,22 +433,22 @@ def _event_ms(torch, stream, fn):
     return e0.elapsed_time(e1)
 
 
-def measure_n34(lp, torch, stream):
-    """The largest Store-zechin order, n = 34 complex: 139 GB of chain tables in HBM
-    (plan budget 150 GB), one seeded matrix of the single-instance kind, against Ryser."""
-    n = 34
-    g = np.random.default_rng(18034)
+def measure_n34(lp, torch, stream, n=34, budget_gb=150):
+    """The largest Store-zechin orders, n = 34 and 35 complex (compact chain tables of 16 B
+    per entry in HBM: 92 and 185 GB), one seeded matrix of the single-instance kind, against
+    Ryser on the same matrix."""
+    g = np.random.default_rng(18000 + n)
     a = ((g.standard_normal((n, n)) + 1j * g.standard_normal((n, n))) / np.sqrt(2.0) / n).astype(np.complex128)
     d = torch.from_numpy(a.reshape(-1)).cuda()
     o = torch.empty(1, dtype=torch.complex128, device="cuda")
     res = {"n": n}
-    for name, meth, budget in (("store_zechin", lp.METHOD_SZ, 150 << 30), ("ryser", lp.METHOD_RYSER, 0)):
+    for name, meth, budget in (("store_zechin", lp.METHOD_SZ, budget_gb << 30), ("ryser", lp.METHOD_RYSER, 0)):
         with lp.Plan(n, "c128", method=meth, max_batch=1, mem_budget_bytes=budget) as p:
             if name == "store_zechin":
                 res["workspace_gb"] = p.workspace_bytes() / 1e9
             res[name + "_ms"] = _event_ms(torch, stream, lambda: p.batch(d, [n], o, None, stream))
             res[name + "_value"] = [float(o[0].real), float(o[0].imag)]
-    res["sz_fp64_tflops"] = sz_c128_flops(n) / (res["store_zechin_ms"] / 1000.0) / 1e12
+    res["sz_work_tflops"] = sz_c128_standard_flops(n) / (res["store_zechin_ms"] / 1000.0) / 1e12
     return res
 
 
@@ -703,7 +704,7 @@ def measure_serving(lp, requests=120, window_s=45.0):
         plat, plat_n, plast = drive_server(srv, preqs, arrivals, window_s + 120.0)
     plain_sat, _ = plain_rate(lp, sat, 900.0)
     plain = serve_plain(lp, preqs, arrivals, window_s + 120.0)
-    return {"n_range": [10, 36], "table_budget": "server default (min(80 GB, free/3))",
+    return {"n_range": [10, 36], "table_budget": "server default (min(100 GB, 40% of free))",
             "saturated": {"requests": len(sat), "served_perm_per_s": served, "plain_perm_per_s": plain_sat,
                           "served_vs_plain": served / plain_sat,
                           "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99)},

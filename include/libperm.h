@@ -14,7 +14,7 @@
  *    primary method.
  *  - Ryser's inclusion-exclusion formula (Section 3.3, Eqs. (2)-(4)) walked in
  *    Gray-code order.  It needs no tables and is the fallback when the
- *    Store-zechin tables do not fit the memory budget (and for n > 34).
+ *    Store-zechin tables do not fit the memory budget (and for n > 35).
  *    For integer matrices it is also the default (PERM_METHOD_AUTO): on a
  *    GB300 its register-resident walk is faster than the integer tables at
  *    every order measured (n = 2..30), while for complex matrices Store-zechin
@@ -38,7 +38,7 @@
  *     offset_i = sum_{j<i} n_j^2 of `mats`.  Device buffers must be aligned to
  *     their element type (16 bytes for complex128 -- as torch and cudaMalloc
  *     give them).
- *   - n = 0 is allowed and gives per = 1 (empty product).  1 <= n <= 34 may use
+ *   - n = 0 is allowed and gives per = 1 (empty product).  1 <= n <= 35 may use
  *     Store-zechin; Ryser accepts n <= 40 (complex) and n <= 40 (integers).
  *   - Results: PERM_C128 -> double2 out[count] (re, im).  Integer types ->
  *     uint64 out[2*count], (low, high) words of a 128-bit unsigned value; with
@@ -189,14 +189,14 @@ perm_status perm_batch_host(perm_plan_t plan, const void *mats, const int *sizes
    Three lanes, by cost, each on streams of its own priority:
      - complex n <= 20 and integer n <= 28: one batch of every pending request
        as soon as the previous batch is done (highest priority);
-     - complex 21 <= n <= 34 whose Store-zechin tables fit mem_budget_bytes:
+     - complex 21 <= n <= 35 whose Store-zechin tables fit mem_budget_bytes:
        up to four jobs at once (a job: requests of one order, up to 16),
-       admitted while the tables of all jobs in flight fit the budget; the
-       tables come from a pool of the budget's size and return to it as each
-       job finishes;
+       admitted first come, first served while a contiguous free range of the
+       budget holds the job's tables; each job's range is freed when the job
+       finishes;
      - every other request with Ryser, batches of up to 64 (lowest priority).
-   Server options: mem_budget_bytes = Store-zechin table budget (0 = min(80 GB,
-   a third of the free memory), reserved at creation); max_batch = queue
+   Server options: mem_budget_bytes = Store-zechin table budget (0 = min(100 GB,
+   40 % of the free memory), reserved at creation); max_batch = queue
    capacity (0 = 65536); flags: PERM_FLAG_WIDE as for plans; the other fields
    are ignored.  Every result is the bits perm_batch gives for that matrix
    (PERM_METHOD_AUTO; PERM_METHOD_RYSER for the Ryser lane). */

@@ -216,7 +216,8 @@ static perm_status plan_create_core(int n_max, perm_dtype dtype, const perm_opts
     if (dtype != PERM_C128) p->m_small = p->m_single;   // integers: one shape (the 256-thread kernel)
     if (o.low_cols) p->m_single = p->m_small = o.low_cols;
     if (shape.m_single >= 1 && shape.m_single <= kMaxLow && !o.low_cols) p->m_small = shape.m_single;
-    if (shape.layer_threads == 384 || shape.layer_threads == 512) p->layer_threads_small = shape.layer_threads;
+    if (shape.layer_threads == 384 || shape.layer_threads == 512 || shape.layer_threads == 768)
+        p->layer_threads_small = shape.layer_threads;
     if (shape.layer_grid_mult >= 1 && shape.layer_grid_mult <= 8) p->layer_grid_small = shape.layer_grid_mult;
     // experiment knobs (results are bit-identical for every choice)
     if (const char* v = getenv("LIBPERM_SZ_LOW")) { int x = atoi(v); if (x >= 1 && x <= kMaxLow) p->m_low = x; }
@@ -228,7 +229,7 @@ static perm_status plan_create_core(int n_max, perm_dtype dtype, const perm_opts
     if (const char* v = getenv("LIBPERM_SZ_TAIL_LAYERS")) p->tail_to_layers = atoi(v) != 0;
     if (const char* v = getenv("LIBPERM_SZ_LAYER_THREADS")) {
         const int x = atoi(v);
-        if (x == 384 || x == 512) p->layer_threads = p->layer_threads_small = x;
+        if (x == 384 || x == 512 || x == 768) p->layer_threads = p->layer_threads_small = x;
     }
     if (const char* v = getenv("LIBPERM_SZ_LAYER_GRID")) {
         const int x = atoi(v);

@@ -16,9 +16,14 @@
 namespace perm {
 
 constexpr int kMaxN = 40;          // largest order any path accepts
-constexpr int kMaxNSZ = 34;        // Store-zechin: C(34,17) < 2^32 keeps ranks 32-bit
+constexpr int kMaxNSZ = 35;        // Store-zechin: chains of 2^13 need t = n - 13 <= kMaxHigh
 constexpr int kMaxLow = 13;        // chain width m (low columns): 2^13 entries fit shared memory
-constexpr int kMaxHigh = 21;       // high columns t = n - m (chain slots and masks stay small)
+constexpr int kMaxHigh = 22;       // high columns t = n - m (binomial tables hold C(x, y), x < 24)
+// From this order on complex chain tables keep (Re, Im) of every entry only, 16 bytes instead of
+// 24: the outer terms recompute w = Re + Im (one FP64 operation more per outer term, about 19 %
+// more work at n = 34) and the tables take two thirds of the memory (n = 34: 92 GB instead of
+// 139 GB; n = 35: 185 GB).  A function of n alone, so results do not depend on the path.
+constexpr int kCompactN = 33;
 
 // Low-column count actually used for an n x n matrix when `m_param` is requested.
 __host__ __device__ inline int sz_low_for(int n, int m_param) {
@@ -207,7 +212,6 @@ __device__ __forceinline__ int width_status(int w) {
 // A chain is the set of all (H, L) with a fixed high subset H and every low
 // subset L; it holds 2^m entries.  Workspace for the chains of one matrix:
 // two layers of C(t, floor(t/2)) chains.
-size_t sz_chain_words(int dtype, int m);                 // 64-bit words per chain
 size_t sz_matrix_workspace_bytes(int dtype, int n, int m);
 int sz_smem_bytes(int dtype, int n, int m);                // dynamic shared memory per CTA
 int sz_batched_occupancy(int dtype, int n_max, int m, int threads);   // resident CTAs per SM
@@ -234,18 +238,18 @@ cudaError_t sz_launch_single(int dtype, const void* mats, long long offset, int 
 // in each layer launch; matrix c of the list uses the workspace slice
 // [c * ws_bytes_per_item, (c + 1) * ws_bytes_per_item), ws_bytes_per_item >=
 // sz_matrix_workspace_bytes(dtype, n, m).
-// threads: CTA size of the complex layer kernel, 384 (two CTAs per SM) or 512 (one; also
-// for 0); every choice gives the same bits.
+// threads: CTA size of the complex layer kernel, 384 (two CTAs per SM), 512 (one; also for 0)
+// or 768 (one); every choice gives the same bits.
 //
 // Default shape of the complex layer path by order (measured on GB300, one matrix alone):
 // up to order 24 chains of 2^12 entries at two 384-thread CTAs per SM (more, smaller chains fill
 // the small first and last layers: n = 24 2.08 ms against 2.56 ms), above it chains of 2^13 at
-// one 512-thread CTA per SM (one outer column fewer, so fewer predecessor loads: n = 28 25.9 ms
-// against 32.3 ms, n = 32 454 ms against 572 ms).
+// one 768-thread CTA per SM (one outer column fewer, so fewer predecessor loads: n = 28 25.7 ms
+// against 32.3 ms, n = 32 449 ms against 572 ms; 512 threads: 26.0 and 455 ms).
 constexpr int kLayerSmallN = 24;
 inline void sz_layer_default_shape(int n, int* m, int* threads) {
     *m = n <= kLayerSmallN ? 12 : 13;
-    *threads = n <= kLayerSmallN ? 384 : 512;
+    *threads = n <= kLayerSmallN ? 384 : 768;
 }
 cudaError_t sz_launch_layers(int dtype, const void* mats, const ItemDesc* items, int count, int n, int m,
                              void* out, int out_words, int* item_status, void* workspace,

@@ -17,9 +17,12 @@
 //               order behind it (they share every layer launch).  A job is
 //               admitted while the tables of all jobs in flight stay within
 //               the budget -- C(t, t/2) chains of 2^12 or 2^13 entries, two
-//               layers, per matrix -- and its tables come from a stream-ordered memory
-//               pool and return to it when the job's kernels finish, so the
-//               next job is admitted as memory frees up.  Middle priority.
+//               layers, per matrix.  Its tables are a contiguous range of
+//               one allocation of the budget's size, made when the server is
+//               created and carved on the host (first fit), and the range
+//               returns when the job's kernels are seen to finish, so the next
+//               job is admitted as memory frees up -- no allocation call on the
+//               worker's path.  Middle priority.
 //   Ryser lane  every other order (Ryser's formula, Section 3.3, which needs no
 //               tables): batches of pending requests, grouped by order inside
 //               one perm_batch, bounded by their number of Gray codes.  Lowest
@@ -39,6 +42,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <deque>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <new>
@@ -93,7 +97,8 @@ struct Slot {
     int out_cap = 0;
     ItemDesc* h_desc = nullptr;      // table slots: descriptors of the job's matrices
     ItemDesc* d_desc = nullptr;
-    size_t ws_bytes = 0;             // table slots: bytes of the job's tables (budget accounting)
+    size_t ws_off = 0;               // table slots: the job's tables in the arena
+    size_t ws_bytes = 0;
     std::vector<Request*> inflight;
     std::vector<size_t> inflight_at;  // byte offset of each in-flight result in h_out
     bool busy = false;
@@ -127,8 +132,8 @@ struct perm_server_s {
     std::thread worker;
     Lane lanes[kLanes];
     size_t table_budget = 0;
-    size_t table_in_use = 0;            // tables of the table jobs in flight (worker thread only)
-    cudaMemPool_t pool = nullptr;       // stream-ordered pool of the table lane
+    unsigned char* arena = nullptr;     // the table lane's memory (table_budget bytes)
+    std::map<size_t, size_t> arena_free; // free ranges of the arena: offset -> bytes (worker only)
     int queue_cap = kQueueCap;
 };
 
@@ -276,11 +281,51 @@ bool plan_launch(perm_server_t s, Lane& L, Slot& S, std::vector<Request*>& batch
     return true;
 }
 
+// The table lane's arena (worker thread only): first-fit ranges of the one
+// allocation, sizes rounded to 256 bytes, neighbours merged when freed.
+constexpr size_t kArenaAlign = 256;
+size_t arena_round(size_t bytes) { return (bytes + kArenaAlign - 1) & ~(kArenaAlign - 1); }
+
+size_t arena_largest(const perm_server_t s) {
+    size_t best = 0;
+    for (const auto& f : s->arena_free) best = std::max(best, f.second);
+    return best;
+}
+
+bool arena_alloc(perm_server_t s, size_t bytes, size_t* off) {
+    bytes = arena_round(bytes);
+    for (auto it = s->arena_free.begin(); it != s->arena_free.end(); ++it) {
+        if (it->second < bytes) continue;
+        *off = it->first;
+        const size_t rest = it->second - bytes, at = it->first + bytes;
+        s->arena_free.erase(it);
+        if (rest) s->arena_free.emplace(at, rest);
+        return true;
+    }
+    return false;
+}
+
+void arena_release(perm_server_t s, size_t off, size_t bytes) {
+    bytes = arena_round(bytes);
+    auto it = s->arena_free.emplace(off, bytes).first;
+    auto next = std::next(it);
+    if (next != s->arena_free.end() && it->first + it->second == next->first) {
+        it->second += next->second;
+        s->arena_free.erase(next);
+    }
+    if (it != s->arena_free.begin()) {
+        auto prev = std::prev(it);
+        if (prev->first + prev->second == it->first) {
+            prev->second += it->second;
+            s->arena_free.erase(it);
+        }
+    }
+}
+
 // Table lane: one job (requests of one order) on the slot's stream, its tables
-// from the pool on the same stream and released behind the job's kernels.
-// Returns 1 on success, 0 if the tables could not be allocated (nothing was
-// launched), -1 on a CUDA error.
-int table_launch(perm_server_t s, Slot& S, std::vector<Request*>& job) {
+// a range of the arena that take_table_job found free.  Returns false on a CUDA
+// error (the range is then returned).
+bool table_launch(perm_server_t s, Slot& S, std::vector<Request*>& job) {
     const int n = job[0]->n;
     const int c = (int)job.size();
     const size_t ws_item = table_bytes(n);
@@ -296,28 +341,29 @@ int table_launch(perm_server_t s, Slot& S, std::vector<Request*>& job) {
         S.inflight.push_back(r);
         S.inflight_at.push_back((size_t)i * 16);
     }
-    void* ws = nullptr;
-    if (cudaMallocFromPoolAsync(&ws, (size_t)c * ws_item, s->pool, S.stream) != cudaSuccess) {
-        cudaGetLastError();
-        S.inflight.clear();
-        S.inflight_at.clear();
-        return 0;
-    }
+    size_t ws_off = 0;
+    if (!arena_alloc(s, (size_t)c * ws_item, &ws_off)) return false;   // take_table_job checked the fit
+    void* ws = s->arena + ws_off;
     bool ok = cudaMemcpyAsync(S.d_in, S.h_in, off, cudaMemcpyHostToDevice, S.stream) == cudaSuccess &&
               cudaMemcpyAsync(S.d_desc, S.h_desc, (size_t)c * sizeof(ItemDesc), cudaMemcpyHostToDevice,
                               S.stream) == cudaSuccess;
     int lm = 0, lthreads = 0;
     sz_layer_default_shape(n, &lm, &lthreads);
+    // one CTA per chain (no CTA loops over several): CTAs retire every chain, so a batch of the
+    // fast lane waits at most a chain's time for SMs, not a whole layer launch's
     if (ok)
         ok = sz_launch_layers(PERM_C128, S.d_in, S.d_desc, c, n, lm, S.d_out, 2, S.d_status, ws, ws_item,
-                              (lthreads == 384 ? 2 : 1) * s->num_sms, S.stream, lthreads) == cudaSuccess;
-    if (cudaFreeAsync(ws, S.stream) != cudaSuccess) ok = false;
+                              1 << 30, S.stream, lthreads) == cudaSuccess;
     if (ok) ok = slot_finish_launch(S, (size_t)c * 16, c);
-    if (!ok) return -1;
+    if (!ok) {
+        arena_release(s, ws_off, (size_t)c * ws_item);
+        return false;
+    }
     for (Request* r : job) r->state.store(1, std::memory_order_relaxed);
+    S.ws_off = ws_off;
     S.ws_bytes = (size_t)c * ws_item;
     S.busy = true;
-    return 1;
+    return true;
 }
 
 void slot_complete(Slot& S) {
@@ -363,11 +409,12 @@ void take_table_job(perm_server_t s, std::vector<Request*>& job) {
     if (q.empty()) return;
     const int n = q.front()->n;
     const size_t ws_item = table_bytes(n);
-    size_t used = s->table_in_use;
+    const size_t avail = arena_largest(s);      // the job's tables are one contiguous range
+    size_t used = 0;
     for (auto it = q.begin(); it != q.end() && (int)job.size() < kTableJob;) {
         Request* r = *it;
         if (r->n != n) { ++it; continue; }
-        if (used + ws_item > s->table_budget) break;
+        if (arena_round(used + ws_item) > avail) break;
         used += ws_item;
         job.push_back(r);
         it = q.erase(it);
@@ -388,7 +435,10 @@ void worker_loop(perm_server_t s) {
                 const cudaError_t q = cudaEventQuery(S.done);
                 if (q == cudaSuccess) {
                     slot_complete(S);
-                    if (li == kLaneTable) { s->table_in_use -= S.ws_bytes; S.ws_bytes = 0; }
+                    if (li == kLaneTable) {   // the job's kernels are done: its tables are free
+                        arena_release(s, S.ws_off, S.ws_bytes);
+                        S.ws_bytes = 0;
+                    }
                     s->busy_slots--;
                     did = true;
                 } else if (q != cudaErrorNotReady) {
@@ -419,17 +469,8 @@ void worker_loop(perm_server_t s) {
                 if (batch.empty()) break;      // nothing (more) this lane can start now
                 did = true;
                 if (li == kLaneTable) {
-                    const int rc = table_launch(s, S, batch);
-                    if (rc == 1) {
-                        s->table_in_use += S.ws_bytes;
+                    if (table_launch(s, S, batch)) {
                         s->busy_slots++;
-                    } else if (rc == 0) {
-                        // the pool could not supply the tables: these requests run with Ryser
-                        std::lock_guard<std::mutex> g(s->mu);
-                        for (auto it = batch.rbegin(); it != batch.rend(); ++it)
-                            s->queues[kLaneRyser].push_front(*it);
-                        s->queued += (int)batch.size();
-                        break;
                     } else {
                         s->failed = true;
                         fail_requests(batch);
@@ -474,9 +515,10 @@ perm_status perm_server_create(const perm_opts* opts, void* stream, perm_server_
         delete s;
         return PERM_ECUDA;
     }
-    // table budget of the table lane: default min(80 GB, a third of the free memory)
+    // table budget of the table lane: default min(100 GB, 40 % of the free memory), which holds
+    // the compact tables of one n = 34 matrix (92.5 GB) on an otherwise idle GB300
     s->table_budget = s->opts.mem_budget_bytes ? s->opts.mem_budget_bytes
-                                               : std::min<size_t>((size_t)80 << 30, free_b / 3);
+                                               : std::min<size_t>((size_t)100 << 30, (size_t)(0.4 * (double)free_b));
     int least = 0, greatest = 0;
     cudaDeviceGetStreamPriorityRange(&least, &greatest);
     Lane& fast = s->lanes[kLaneFast];
@@ -500,25 +542,9 @@ perm_status perm_server_create(const perm_opts* opts, void* stream, perm_server_
               slot_alloc(ryser.slots[0], ryser.priority, (size_t)kRyserBatch * kMaxN * kMaxN * 16, kRyserBatch, 0);
     for (Slot& S : table.slots)
         if (ok) ok = slot_alloc(S, table.priority, (size_t)kTableJob * kMaxNSZ * kMaxNSZ * 16, kTableJob, kTableJob);
-    // the table lane's pool: memory stays reserved up to the budget (release threshold) and is
-    // reused by later jobs once the jobs that freed it are seen to be complete
-    if (ok) {
-        cudaMemPoolProps props{};
-        props.allocType = cudaMemAllocationTypePinned;
-        props.location.type = cudaMemLocationTypeDevice;
-        props.location.id = s->device;
-        ok = cudaMemPoolCreate(&s->pool, &props) == cudaSuccess;
-        unsigned long long thr = s->table_budget;
-        int no = 0;
-        if (ok) ok = cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &thr) == cudaSuccess;
-        if (ok) ok = cudaMemPoolSetAttribute(s->pool, cudaMemPoolReuseAllowInternalDependencies, &no) == cudaSuccess;
-        // reserve the budget now: one allocation of all of it, returned to the pool
-        void* p = nullptr;
-        cudaStream_t st0 = table.slots[0].stream;
-        if (ok) ok = cudaMallocFromPoolAsync(&p, s->table_budget, s->pool, st0) == cudaSuccess;
-        if (ok) ok = cudaFreeAsync(p, st0) == cudaSuccess;
-        if (ok) ok = cudaStreamSynchronize(st0) == cudaSuccess;
-    }
+    // the table lane's arena: all of the budget, allocated once
+    if (ok) ok = cudaMalloc(&s->arena, s->table_budget) == cudaSuccess;
+    if (ok) s->arena_free.emplace(0, s->table_budget & ~(kArenaAlign - 1));
     // the plans now (they load their kernels): creating one, or loading a kernel, while another
     // lane's work runs could wait for that work; the table lane's kernels are loaded here too
     for (int dt : {PERM_C128, PERM_U01, PERM_I64}) {
@@ -529,7 +555,7 @@ perm_status perm_server_create(const perm_opts* opts, void* stream, perm_server_
     if (!ok) {
         cudaGetLastError();
         for (auto& L : s->lanes) lane_free(L);
-        if (s->pool) cudaMemPoolDestroy(s->pool);
+        if (s->arena) cudaFree(s->arena);
         delete s;
         return PERM_ENOMEM;
     }
@@ -612,7 +638,7 @@ perm_status perm_server_destroy(perm_server_t s, int timeout_ms) {
     }
     s->worker.join();
     for (auto& L : s->lanes) lane_free(L);
-    if (s->pool) cudaMemPoolDestroy(s->pool);
+    if (s->arena) cudaFree(s->arena);
     delete s;
     return result;
 }

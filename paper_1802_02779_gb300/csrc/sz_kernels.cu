@@ -170,6 +170,9 @@ __device__ __forceinline__ void chain_setup(const MatCtx& mc, unsigned Hmask, in
 // read from shared memory.  Outer columns are 0..t-1 and chain columns t..n-1,
 // so the accumulation order is all columns ascending.
 // ---------------------------------------------------------------------------
+// COMPACT (orders >= kCompactN): global chains hold the uv plane only, and the outer
+// phase recomputes w = u + v for each predecessor entry it loads.
+template <bool COMPACT>
 __device__ void chain_c128(const MatCtx& mc, int s, unsigned char* chain_smem, const double* gprev,
                            double* gdst, const unsigned char* coef_smem, bool last, double2* out,
                            int out_index) {
@@ -180,6 +183,8 @@ __device__ void chain_c128(const MatCtx& mc, int s, unsigned char* chain_smem, c
     const double2* cxy = reinterpret_cast<const double2*>(coef_smem);
     const double* cs = reinterpret_cast<const double*>(coef_smem + 16 * n * n);
     const unsigned* bn = mc.bn;
+    constexpr bool compact = COMPACT;
+    const size_t cwd = (compact ? 2 : 3) * (size_t)CL;          // doubles per global chain
     const int* hslot = mc.hinfo;
     const int* hcol = mc.hinfo + kBinomDim;
     const unsigned short* masks = mc.masks;
@@ -199,9 +204,10 @@ __device__ void chain_c128(const MatCtx& mc, int s, unsigned char* chain_smem, c
 #pragma unroll
                 for (int z = 0; z < 4; z++) {
                     if (q + z < s) {
-                        const double* pc = gprev + (size_t)hslot[q + z] * 3 * CL;
+                        const double* pc = gprev + (size_t)hslot[q + z] * cwd;
                         huv[z] = __ldg(reinterpret_cast<const double2*>(pc) + idx);
-                        hw[z] = __ldg(pc + 2 * CL + idx);
+                        // compact tables: w = u + v, rounded once, recomputed here
+                        hw[z] = compact ? __fma_rn(huv[z].x, 1.0, huv[z].y) : __ldg(pc + 2 * CL + idx);
                     }
                 }
 #pragma unroll
@@ -243,7 +249,7 @@ __device__ void chain_c128(const MatCtx& mc, int s, unsigned char* chain_smem, c
                 const double2* fxy = cxy + (n - 1) * n;
                 dd2 re = {0.0, 0.0}, im = {0.0, 0.0};
                 for (int q = 0; q < s; q++) {
-                    const double2 p = reinterpret_cast<const double2*>(gprev + (size_t)hslot[q] * 3 * CL)[idx];
+                    const double2 p = reinterpret_cast<const double2*>(gprev + (size_t)hslot[q] * cwd)[idx];
                     const double2 c = fxy[hcol[q]];
                     re = dd_add_prod(re, c.x, p.x);
                     re = dd_add_prod(re, -c.y, p.y);
@@ -291,7 +297,7 @@ __device__ void chain_c128(const MatCtx& mc, int s, unsigned char* chain_smem, c
             sw[mask] = w;
             if (gdst) {
                 reinterpret_cast<double2*>(gdst)[idx] = make_double2(u, v);
-                gdst[2 * CL + idx] = w;
+                if (!compact) gdst[2 * CL + idx] = w;
             }
             if (last && l == m) out[out_index] = make_double2(u, v);
         }
@@ -467,19 +473,19 @@ __device__ inline void init_ctx(MatCtx& mc, int n, int m_param, const unsigned c
     mc.out_words = 2;
 }
 
-// Global-memory words of one chain.
-__host__ __device__ inline size_t chain_words(int kind, int m) {
-    return (size_t)(kind == kC128 ? 3 : (kind == kU64 ? 1 : 2)) << m;
+// Global-memory words of one chain (complex: 2 per entry in compact tables, else 3).
+__host__ __device__ inline size_t chain_words(int kind, int m, bool compact = false) {
+    return (size_t)(kind == kC128 ? (compact ? 2 : 3) : (kind == kU64 ? 1 : 2)) << m;
 }
 
-// One chain of a matrix, any element kind.
-template <int KIND, bool ZO>
+// One chain of a matrix, any element kind (COMPACT: complex compact tables).
+template <int KIND, bool ZO, bool COMPACT = false>
 __device__ __forceinline__ void run_chain(const MatCtx& mc, int s, unsigned char* smem_chain,
                                           const unsigned long long* src, unsigned long long* dst,
                                           const unsigned char* coef, bool last, void* out,
                                           int out_index) {
     if (KIND == kC128)
-        chain_c128(mc, s, smem_chain, reinterpret_cast<const double*>(src),
+        chain_c128<COMPACT>(mc, s, smem_chain, reinterpret_cast<const double*>(src),
                    reinterpret_cast<double*>(dst), coef, last, reinterpret_cast<double2*>(out),
                    out_index);
     else
@@ -493,7 +499,7 @@ __device__ __forceinline__ void run_chain(const MatCtx& mc, int s, unsigned char
 template <int KIND, bool ZO>
 __device__ void run_matrix_cta(const MatCtx& mc, unsigned char* smem_chain, unsigned long long* ws,
                                const unsigned char* coef, void* out, int out_index, int* hinfo) {
-    const size_t CW = chain_words(KIND, mc.m);
+    const size_t CW = chain_words(KIND, mc.m);     // batched matrices are below kCompactN
     const size_t layer_words = (size_t)binom_calc(mc.t, mc.t / 2) * CW;
     for (int s = 0; s <= mc.t; s++) {
         const unsigned nslots = (unsigned)binom_calc(mc.t, s);
@@ -590,7 +596,7 @@ sz_batched_int(const long long* __restrict__ mats, const ItemDesc* __restrict__ 
 // Each chain is computed exactly as in the batched kernels, so results do not
 // depend on how many matrices share a launch.
 // ---------------------------------------------------------------------------
-template <int THREADS>
+template <int THREADS, bool COMPACT>
 __global__ void __launch_bounds__(THREADS, THREADS <= 384 ? 2 : 1)
 sz_layer_c128(const double2* __restrict__ mats, const ItemDesc* __restrict__ items, ItemDesc single,
               int count, int n, int m_param, int s, double2* out, int* item_status,
@@ -600,7 +606,7 @@ sz_layer_c128(const double2* __restrict__ mats, const ItemDesc* __restrict__ ite
     const SmemLayout L = smem_layout(kC128, n, sz_low_for(n, m_param));
     MatCtx mc;
     init_ctx(mc, n, m_param, smem, L);
-    const size_t CW = chain_words(kC128, mc.m);
+    const size_t CW = chain_words(kC128, mc.m, COMPACT);
     const size_t layer_words = (size_t)binom_calc(mc.t, mc.t / 2) * CW;
     const unsigned nslots = (unsigned)binom_calc(mc.t, s);
     const bool last = (s == mc.t);
@@ -620,9 +626,9 @@ sz_layer_c128(const double2* __restrict__ mats, const ItemDesc* __restrict__ ite
         const unsigned long long* src_region = ws + (size_t)((s + 1) & 1) * layer_words;
         chain_setup(mc, unrank_high(slot, s, mc.t, mc.bn), reinterpret_cast<int*>(smem + L.hinfo_off));
         __syncthreads();
-        run_chain<kC128, false>(mc, s, smem + L.chain_off, src_region,
-                                last ? nullptr : dst_region + (size_t)slot * CW, smem + L.coef_off,
-                                last, out, d.out_index);
+        run_chain<kC128, false, COMPACT>(mc, s, smem + L.chain_off, src_region,
+                                         last ? nullptr : dst_region + (size_t)slot * CW, smem + L.coef_off,
+                                         last, out, d.out_index);
         if (last && threadIdx.x == 0 && item_status) item_status[d.out_index] = PERM_OK;
     }
 }
@@ -775,16 +781,13 @@ cudaError_t sz_init_tables() {
     return e;
 }
 
-size_t sz_chain_words(int dtype, int m) {
-    // integer chains are sized for 128-bit entries
-    return chain_words(dtype == PERM_C128 ? kC128 : kU128, m);
-}
-
 size_t sz_matrix_workspace_bytes(int dtype, int n, int m_param) {
     const int m = sz_low_for(n, m_param);
     const int t = n - m;
     if (t <= 0) return 0;
-    return 2 * (size_t)binom_calc(t, t / 2) * sz_chain_words(dtype, m) * 8;
+    // integer chains are sized for 128-bit entries
+    const size_t cw = dtype == PERM_C128 ? chain_words(kC128, m, n >= kCompactN) : chain_words(kU128, m);
+    return 2 * (size_t)binom_calc(t, t / 2) * cw * 8;
 }
 
 int sz_smem_bytes(int dtype, int n, int m_param) {
@@ -799,10 +802,13 @@ static const void* c128_batched_fn(int threads) {
     switch (threads) {
         case 256: return (const void*)sz_batched_c128<256>;
         case 512: return (const void*)sz_batched_c128<512>;
+        case 768: return (const void*)sz_batched_c128<768>;
         default: return (const void*)sz_batched_c128<384>;
     }
 }
-int sz_c128_threads_valid(int threads) { return threads == 256 || threads == 384 || threads == 512; }
+int sz_c128_threads_valid(int threads) {
+    return threads == 256 || threads == 384 || threads == 512 || threads == 768;
+}
 int sz_int_threads_valid(int threads) { return threads == 256 || threads == 512; }
 
 // Resident CTAs per SM of the batched kernel for a batch whose largest order is n_max.
@@ -842,6 +848,8 @@ cudaError_t sz_launch_batched(int dtype, const void* mats, const ItemDesc* items
             sz_batched_c128<256><<<grid, 256, smem, st>>>(a0, items, count, m, o0, item_status, w0, wpc, counter);
         else if (threads == 512)
             sz_batched_c128<512><<<grid, 512, smem, st>>>(a0, items, count, m, o0, item_status, w0, wpc, counter);
+        else if (threads == 768)
+            sz_batched_c128<768><<<grid, 768, smem, st>>>(a0, items, count, m, o0, item_status, w0, wpc, counter);
         else
             sz_batched_c128<384><<<grid, 384, smem, st>>>(a0, items, count, m, o0, item_status, w0, wpc, counter);
     } else {
@@ -858,6 +866,16 @@ cudaError_t sz_launch_batched(int dtype, const void* mats, const ItemDesc* items
 
 namespace {
 
+typedef void (*c128_layer_fn)(const double2*, const ItemDesc*, ItemDesc, int, int, int, int, double2*, int*,
+                              unsigned long long*, size_t);
+
+// The complex layer kernel for a CTA size (384, 512 or 768; others: 512) and table kind.
+c128_layer_fn pick_c128_layer(int threads, bool compact) {
+    if (threads == 384) return compact ? sz_layer_c128<384, true> : sz_layer_c128<384, false>;
+    if (threads == 768) return compact ? sz_layer_c128<768, true> : sz_layer_c128<768, false>;
+    return compact ? sz_layer_c128<kThreadsC128Single, true> : sz_layer_c128<kThreadsC128Single, false>;
+}
+
 // Layers 0..t of `count` matrices of order n (items on the device, or one
 // matrix `single` when items == nullptr).
 cudaError_t sz_launch_layers_impl(int dtype, const void* mats, const ItemDesc* items, ItemDesc single,
@@ -868,23 +886,19 @@ cudaError_t sz_launch_layers_impl(int dtype, const void* mats, const ItemDesc* i
     const int mm = sz_low_for(n, m);
     const int t = n - mm;
     const int smem = sz_smem_bytes(dtype, n, m);
-    const bool c384 = threads == 384;
-    const void* fn = dtype == PERM_C128 ? (c384 ? (const void*)sz_layer_c128<384> : (const void*)sz_layer_c128<512>)
+    const c128_layer_fn cfn = pick_c128_layer(threads, n >= kCompactN);
+    const void* fn = dtype == PERM_C128 ? (const void*)cfn
                    : (dtype == PERM_U01 ? (const void*)sz_layer_int<true> : (const void*)sz_layer_int<false>);
     cudaError_t e = set_smem(fn, smem);
     if (e != cudaSuccess) return e;
     const size_t wpi = ws_bytes_per_item / 8;
+    const int cthreads = threads == 384 || threads == 768 ? threads : kThreadsC128Single;
     for (int s = 0; s <= t; s++) {
         const unsigned long long tasks = binom_calc(t, s) * (unsigned long long)count;
         const int grid = (int)std::min<unsigned long long>(tasks, (unsigned long long)grid_cap);
-        if (dtype == PERM_C128 && c384) {
-            sz_layer_c128<384><<<grid, 384, smem, st>>>(
-                (const double2*)mats, items, single, count, n, m, s, (double2*)out, item_status,
-                (unsigned long long*)workspace, wpi);
-        } else if (dtype == PERM_C128) {
-            sz_layer_c128<kThreadsC128Single><<<grid, kThreadsC128Single, smem, st>>>(
-                (const double2*)mats, items, single, count, n, m, s, (double2*)out, item_status,
-                (unsigned long long*)workspace, wpi);
+        if (dtype == PERM_C128) {
+            cfn<<<grid, cthreads, smem, st>>>((const double2*)mats, items, single, count, n, m, s, (double2*)out,
+                                              item_status, (unsigned long long*)workspace, wpi);
         } else if (dtype == PERM_U01) {
             sz_layer_int<true><<<grid, kThreadsInt, smem, st>>>(
                 (const long long*)mats, items, single, count, n, m, s, (unsigned long long*)out, out_words,
@@ -918,15 +932,16 @@ cudaError_t sz_launch_single(int dtype, const void* mats, long long offset, int 
 
 cudaError_t sz_preload(int dtype) {
     cudaFuncAttributes fa;
-    const void* fns[8];
+    const void* fns[12];
     int k = 0;
     fns[k++] = (const void*)trivial_kernel;
     if (dtype == PERM_C128) {
         fns[k++] = c128_batched_fn(256);
         fns[k++] = c128_batched_fn(384);
         fns[k++] = c128_batched_fn(512);
-        fns[k++] = (const void*)sz_layer_c128<384>;
-        fns[k++] = (const void*)sz_layer_c128<kThreadsC128Single>;
+        fns[k++] = c128_batched_fn(768);
+        for (int threads : {384, 512, 768})
+            for (bool compact : {false, true}) fns[k++] = (const void*)pick_c128_layer(threads, compact);
     } else {
         for (int n_max : {20, 34})
             for (int threads : {256, 512}) fns[k++] = (const void*)pick_int_batched(dtype, n_max, threads);

@@ -143,11 +143,41 @@ def test_serving_alone_vs_mix_large_orders(lp):
     assert [r[0] for r in res[2:]] == list(alone)
 
 
+@pytest.mark.parametrize("n,budget_gb", [(33, 60), (34, 100), (35, 200)])
+def test_store_zechin_compact_tables(lp, n, budget_gb):
+    """Orders 33..35 keep compact chain tables (Re, Im of each entry; w = Re + Im
+    recomputed for outer terms): n = 35 needs 185 GB.  Pinned by the oracle through
+    a block-diagonal matrix, per(B + C) = per(B) per(C), and by the rank-one closed
+    form per(x y^T) = n! prod x prod y."""
+    import math
+    h = n // 2
+    g = np.random.default_rng(3500 + n)
+    b = (g.standard_normal((h, h)) + 1j * g.standard_normal((h, h))) / np.sqrt(2 * h)
+    c = (g.standard_normal((n - h, n - h)) + 1j * g.standard_normal((n - h, n - h))) / np.sqrt(2 * (n - h))
+    blk = np.zeros((n, n), dtype=np.complex128)
+    blk[:h, :h] = b
+    blk[h:, h:] = c
+    x = (g.standard_normal(n) + 1j * g.standard_normal(n)) / 2
+    y = (g.standard_normal(n) + 1j * g.standard_normal(n)) / 2
+    r1 = np.outer(x, y)
+    with lp.Plan(n, "c128", method=lp.METHOD_SZ, max_batch=2, mem_budget_bytes=budget_gb << 30) as p:
+        d = p.describe()
+        assert d["sz_single_nmax"] == n
+        assert p.workspace_bytes() < (budget_gb << 30)
+        got, st = lp.permanents([blk, r1], "c128", plan=p, return_status=True)
+    assert list(st) == [lp.PERM_OK, lp.PERM_OK]
+    want_blk = oracle_c(b) * oracle_c(c)
+    scale_blk = oracle.per_abs(b) * oracle.per_abs(c)
+    assert abs(got[0] - want_blk) <= 1e-12 * scale_blk, (got[0], want_blk)
+    want_r1 = math.factorial(n) * np.prod(x) * np.prod(y)
+    scale_r1 = math.factorial(n) * np.prod(np.abs(x)) * np.prod(np.abs(y))
+    assert abs(got[1] - want_r1) <= 1e-12 * scale_r1, (got[1], want_r1)
+
+
 def test_store_zechin_n34_in_hbm(lp):
-    """The largest Store-zechin order: n = 34 complex, 139 GB of chain tables in HBM
-    (a 150 GB budget).  Pinned by the oracle through a block-diagonal matrix,
-    per(B + C) = per(B) per(C) with 17 x 17 blocks, and by the rank-one closed form
-    per(x y^T) = n! prod x prod y."""
+    """n = 34 complex in compact chain tables (92 GB of HBM, a 150 GB budget).
+    Pinned by the oracle through a block-diagonal matrix, per(B + C) = per(B) per(C)
+    with 17 x 17 blocks, and by the rank-one closed form per(x y^T) = n! prod x prod y."""
     import math
     n, h = 34, 17
     g = np.random.default_rng(3434)

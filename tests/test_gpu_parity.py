@@ -244,7 +244,7 @@ def test_autotuned_crossover_and_layer_shape_same_bits(lp, tmp_path, monkeypatch
         assert 18 <= d["sz_batch_nmax"] <= 22
         assert (d["layer_cta_threads_small"], d["chain_width_layer_small"]) in ((512, 13), (384, 12), (512, 12))
         assert d["layer_ctas_per_sm_small"] in (1, 2, 4)
-        assert (d["layer_cta_threads"], d["chain_width_single"]) == (512, 13)
+        assert (d["layer_cta_threads"], d["chain_width_single"]) == (768, 13)
         tuned = lp.permanents(mats, "c128", plan=pt)
     assert "perm-tune2" in (tmp_path / "tune.txt").read_text()
     with lp.Plan(24, "c128", max_batch=len(mats)) as p0:
