@@ -194,7 +194,8 @@ perm_status perm_batch_host(perm_plan_t plan, const void *mats, const int *sizes
        admitted first come, first served while a contiguous free range of the
        budget holds the job's tables; each job's range is freed when the job
        finishes;
-     - every other request with Ryser, batches of up to 64 (lowest priority).
+     - every other request with Ryser, batches of up to 64 requests and about
+       0.7 s of work (a larger request runs alone; lowest priority).
    Server options: mem_budget_bytes = Store-zechin table budget (0 = min(100 GB,
    40 % of the free memory), reserved at creation); max_batch = queue
    capacity (0 = 65536); flags: PERM_FLAG_WIDE as for plans; the other fields

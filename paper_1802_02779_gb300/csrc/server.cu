@@ -64,7 +64,10 @@ constexpr int kFastBatch = 4096;
 constexpr int kTableSlots = 4;           // table-lane jobs in flight at once
 constexpr int kTableJob = 16;            // requests of one order per table job
 constexpr int kRyserBatch = 64;
-constexpr double kRyserBatchCodes = 34359738368.0;   // 2^35 Gray codes per Ryser batch (>= 1 request)
+// A Ryser batch holds requests up to 2^31 complex-code equivalents of work (about 0.7 s; a
+// larger request runs alone): every request of a batch completes with the batch, so a large
+// request must not hold small ones back.  An integer code costs about a tenth of a complex one.
+constexpr double kRyserBatchCodes = 2147483648.0;
 constexpr size_t kResultSlot = 32;       // bytes reserved per result in the slot buffers
 
 enum { kLaneFast = 0, kLaneTable = 1, kLaneRyser = 2, kLanes = 3 };
@@ -224,9 +227,10 @@ int table_low(int n) {
 }
 size_t table_bytes(int n) { return sz_matrix_workspace_bytes(PERM_C128, n, table_low(n)); }
 
-// Gray codes Ryser walks for one request (the Ryser lane's batch bound).
+// Work of one request on the Ryser lane in complex-code equivalents (the batch bound).
 double ryser_codes(const Request* r) {
-    return std::ldexp(1.0, r->dtype == PERM_I64 ? r->n : std::max(0, r->n - 1));
+    const double codes = std::ldexp(1.0, r->dtype == PERM_I64 ? r->n : std::max(0, r->n - 1));
+    return r->dtype == PERM_C128 ? codes : 0.1 * codes;
 }
 
 // Copy results back and record the slot's completion event.
