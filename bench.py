@@ -393,7 +393,7 @@ def measure_extras(lp, torch, cm, im, stream, c_kernel_ms, count):
         "batched_complex_perm_per_s": count / (c_kernel_ms / 1000.0),
         "speedup": (count / c_kernel_ms) / (sample / plain_ms),
         "plain_sample": sample,
-        "plain": "one matrix at a time, Store-zechin chain layers over the whole GPU (8 launches per matrix)"}
+        "plain": "one matrix at a time, Store-zechin chain layers over the whole GPU (chains of 2^11: 10 launches per matrix)"}
     # single n = 32 instance, both kernels
     from paper_1802_02779_gb300 import workloads as wl
     a32 = wl.single_n32()

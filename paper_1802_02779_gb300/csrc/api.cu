@@ -66,6 +66,7 @@ struct perm_plan_s {
     int m_small = 12;
     int layer_threads_small = 384;
     int layer_grid_small = 2;
+    int m_few = 11;               // orders up to kLayerSmallN with at most kLayerFewCount matrices
     bool tail_to_layers = true;   // the batched kernel's last partial round takes the layer path
     int c128_threads = 384;       // CTA size of the batched complex kernel
     int int_threads = 256;        // CTA size of the batched integer kernel
@@ -136,8 +137,11 @@ int sz_batch_limit(perm_plan_t p, int complex_cap = 20) {
     return best;
 }
 
-// Chain width of the layer path for order n.
-int layer_m(perm_plan_t p, int n) { return n <= kLayerSmallN ? p->m_small : p->m_single; }
+// Chain width of the layer path for order n, with `count` matrices of that order in a launch.
+int layer_m(perm_plan_t p, int n, int count = kLayerFewCount + 1) {
+    if (n > kLayerSmallN) return p->m_single;
+    return count <= kLayerFewCount ? p->m_few : p->m_small;
+}
 
 }  // namespace
 
@@ -211,10 +215,12 @@ static perm_status plan_create_core(int n_max, perm_dtype dtype, const perm_opts
     p->out_words = (o.flags & PERM_FLAG_WIDE) ? 4 : 2;
     p->max_batch = o.max_batch ? o.max_batch : 65536;
     p->m_low = o.low_cols ? o.low_cols : 12;
-    sz_layer_default_shape(kLayerSmallN + 1, &p->m_single, &p->layer_threads);
-    sz_layer_default_shape(kLayerSmallN, &p->m_small, &p->layer_threads_small);
-    if (dtype != PERM_C128) p->m_small = p->m_single;   // integers: one shape (the 256-thread kernel)
-    if (o.low_cols) p->m_single = p->m_small = o.low_cols;
+    int few_threads = 0;
+    sz_layer_default_shape(kLayerSmallN + 1, kLayerFewCount + 1, &p->m_single, &p->layer_threads);
+    sz_layer_default_shape(kLayerSmallN, kLayerFewCount + 1, &p->m_small, &p->layer_threads_small);
+    sz_layer_default_shape(kLayerSmallN, 1, &p->m_few, &few_threads);
+    if (dtype != PERM_C128) p->m_small = p->m_few = p->m_single;   // integers: one shape (the 256-thread kernel)
+    if (o.low_cols) p->m_single = p->m_small = p->m_few = o.low_cols;
     if (shape.m_single >= 1 && shape.m_single <= kMaxLow && !o.low_cols) p->m_small = shape.m_single;
     if (shape.layer_threads == 384 || shape.layer_threads == 512 || shape.layer_threads == 768)
         p->layer_threads_small = shape.layer_threads;
@@ -270,7 +276,8 @@ static perm_status plan_create_core(int n_max, perm_dtype dtype, const perm_opts
         sz_batched = p->sz_ws_per_cta * (size_t)p->sz_grid;
         // largest n whose single-matrix workspace fits the remaining budget
         for (int n = 1; n <= std::min(n_max, kMaxNSZ); n++) {
-            const size_t need = sz_matrix_workspace_bytes(dtype, n, layer_m(p, n));
+            const size_t need = std::max(sz_matrix_workspace_bytes(dtype, n, layer_m(p, n)),
+                                         sz_matrix_workspace_bytes(dtype, n, layer_m(p, n, 1)));
             if (need + (size_t)(1 << 20) <= p->budget) {
                 p->sz_single_nmax = n;
                 sz_single = std::max(sz_single, need);
@@ -361,12 +368,13 @@ int perm_plan_describe(perm_plan_t p, char* buf, size_t len) {
                     "\"sz_batch_nmax\": %d, \"sz_single_nmax\": %d, \"chain_width_batched\": %d, "
                     "\"chain_width_single\": %d, \"cta_threads\": %d, \"batched_grid\": %d, "
                     "\"layer_cta_threads\": %d, \"layer_ctas_per_sm\": %d, \"layer_small_nmax\": %d, "
+                    "\"chain_width_layer_few\": %d, "
                     "\"chain_width_layer_small\": %d, \"layer_cta_threads_small\": %d, "
                     "\"layer_ctas_per_sm_small\": %d, "
                     "\"workspace_bytes\": %zu, \"out_words\": %d, \"autotuned\": %s}",
                     dt, p->n_max, p->method, p->flags, p->sz_batch_nmax, p->sz_single_nmax, p->m_low,
                     p->m_single, p->dtype == PERM_C128 ? p->c128_threads : p->int_threads, p->sz_grid,
-                    p->dtype == PERM_C128 ? p->layer_threads : 256, p->layer_grid_mult, kLayerSmallN,
+                    p->dtype == PERM_C128 ? p->layer_threads : 256, p->layer_grid_mult, kLayerSmallN, p->m_few,
                     p->m_small, p->dtype == PERM_C128 ? p->layer_threads_small : 256, p->layer_grid_small,
                     perm_plan_workspace_bytes(p), p->dtype == PERM_C128 ? 0 : p->out_words,
                     p->tuned ? "true" : "false");
@@ -477,9 +485,13 @@ perm_status enqueue(perm_plan_t p, const BatchLayout& L, const void* mats, const
         // most of the GPU idle, several fill it.  Two CTAs' worth of chains per SM and
         // layer amortise the per-CTA set-up, and every layer is its own launch, which gives
         // the scheduler a point to interleave work from higher-priority streams.
-        const int lm = layer_m(p, g.n);
+        int lm = layer_m(p, g.n, plain ? 1 : g.cnt);
         const bool small = g.n <= kLayerSmallN;
-        const size_t ws_item = sz_matrix_workspace_bytes(p->dtype, g.n, lm);
+        size_t ws_item = sz_matrix_workspace_bytes(p->dtype, g.n, lm);
+        if (ws_item > p->ws_bytes) {           // the workspace was sized for the batch shape
+            lm = layer_m(p, g.n);
+            ws_item = sz_matrix_workspace_bytes(p->dtype, g.n, lm);
+        }
         long long per_launch = ws_item ? (long long)(p->ws_bytes / ws_item) : (long long)g.cnt;
         per_launch = std::max<long long>(1, per_launch);
         if (plain) per_launch = 1;
@@ -877,7 +889,8 @@ static perm_status plan_create_tuned(int n_max, perm_dtype dtype, const perm_opt
                 else break;
             }
             best.shape.batch_nmax = cross;
-            // (3) the layer path's shape for orders up to kLayerSmallN, on one matrix of order nbig
+            // (3) the layer path's shape for orders up to kLayerSmallN, on four matrices of order nbig
+            // (one or two matrices take the narrower chains of m_few)
             const int cand[4][3] = {{384, 12, 2}, {384, 12, 4}, {512, 13, 1}, {512, 12, 2}};
             float lbest = 0.f;
             for (const auto& c : cand) {
@@ -885,7 +898,7 @@ static perm_status plan_create_tuned(int n_max, perm_dtype dtype, const perm_opt
                 sh.layer_threads = c[0];
                 sh.m_single = c[1];
                 sh.layer_grid_mult = c[2];
-                const float ms = time_shape(nbig, dtype, o, sh, nbig, dm, 1, dout, st);
+                const float ms = time_shape(nbig, dtype, o, sh, nbig, dm, kLayerFewCount + 2, dout, st);
                 if (ms > 0.f && (lbest == 0.f || ms < lbest)) {
                     lbest = ms;
                     best.shape.layer_threads = c[0];

@@ -241,15 +241,19 @@ cudaError_t sz_launch_single(int dtype, const void* mats, long long offset, int 
 // threads: CTA size of the complex layer kernel, 384 (two CTAs per SM), 512 (one; also for 0)
 // or 768 (one); every choice gives the same bits.
 //
-// Default shape of the complex layer path by order (measured on GB300, one matrix alone):
-// up to order 24 chains of 2^12 entries at two 384-thread CTAs per SM (more, smaller chains fill
-// the small first and last layers: n = 24 2.08 ms against 2.56 ms), above it chains of 2^13 at
-// one 768-thread CTA per SM (one outer column fewer, so fewer predecessor loads: n = 28 25.7 ms
-// against 32.3 ms, n = 32 449 ms against 572 ms; 512 threads: 26.0 and 455 ms).
+// Default shape of the complex layer path by order and by the number of matrices of that order
+// in one launch (measured on GB300): up to order 24, chains of 2^12 entries at two 384-thread
+// CTAs per SM, since more and smaller chains fill the narrow first and last layers (one n = 24
+// matrix 2.08 ms against 2.56 ms with 2^13), and for one or two matrices chains of 2^11, whose
+// shorter chains shorten the critical path through the t + 1 layers (one n = 20 matrix 0.48 ms
+// against 0.63; n = 23 1.24 against 1.40); above order 24 chains of 2^13 at one 768-thread CTA
+// per SM, since one outer column fewer means fewer predecessor loads (n = 28 25.6 ms against
+// 32.3 ms, n = 32 447 ms against 572 ms).
 constexpr int kLayerSmallN = 24;
-inline void sz_layer_default_shape(int n, int* m, int* threads) {
-    *m = n <= kLayerSmallN ? 12 : 13;
-    *threads = n <= kLayerSmallN ? 384 : 768;
+constexpr int kLayerFewCount = 2;
+inline void sz_layer_default_shape(int n, int count, int* m, int* threads) {
+    *m = n > kLayerSmallN ? 13 : (count <= kLayerFewCount ? 11 : 12);
+    *threads = n > kLayerSmallN ? 768 : 384;
 }
 cudaError_t sz_launch_layers(int dtype, const void* mats, const ItemDesc* items, int count, int n, int m,
                              void* out, int out_words, int* item_status, void* workspace,

@@ -217,15 +217,17 @@ perm_plan_t lane_plan(perm_server_t s, Lane& L, int dtype) {
     return L.plans[k];
 }
 
-// Table bytes of one complex matrix of order n on the table lane.
-// Table bytes of one complex matrix of order n on the table lane (the layer path's default
-// shape for that order).
-int table_low(int n) {
+// Table bytes of a job of `count` complex matrices of order n on the table lane (the layer
+// path's default shape for that order and count).
+int table_low(int n, int count) {
     int m = 0, threads = 0;
-    sz_layer_default_shape(n, &m, &threads);
+    sz_layer_default_shape(n, count, &m, &threads);
     return m;
 }
-size_t table_bytes(int n) { return sz_matrix_workspace_bytes(PERM_C128, n, table_low(n)); }
+size_t table_item_bytes(int n, int count) { return sz_matrix_workspace_bytes(PERM_C128, n, table_low(n, count)); }
+size_t table_bytes(int n, int count) { return (size_t)count * table_item_bytes(n, count); }
+// The most one matrix of order n can take (admission to the table lane).
+size_t table_bytes_max(int n) { return std::max(table_item_bytes(n, 1), table_item_bytes(n, kLayerFewCount + 1)); }
 
 // Work of one request on the Ryser lane in complex-code equivalents (the batch bound).
 double ryser_codes(const Request* r) {
@@ -332,7 +334,7 @@ void arena_release(perm_server_t s, size_t off, size_t bytes) {
 bool table_launch(perm_server_t s, Slot& S, std::vector<Request*>& job) {
     const int n = job[0]->n;
     const int c = (int)job.size();
-    const size_t ws_item = table_bytes(n);
+    const size_t ws_item = table_item_bytes(n, c);
     S.inflight.clear();
     S.inflight_at.clear();
     size_t off = 0;
@@ -352,7 +354,7 @@ bool table_launch(perm_server_t s, Slot& S, std::vector<Request*>& job) {
               cudaMemcpyAsync(S.d_desc, S.h_desc, (size_t)c * sizeof(ItemDesc), cudaMemcpyHostToDevice,
                               S.stream) == cudaSuccess;
     int lm = 0, lthreads = 0;
-    sz_layer_default_shape(n, &lm, &lthreads);
+    sz_layer_default_shape(n, c, &lm, &lthreads);
     // one CTA per chain (no CTA loops over several): CTAs retire every chain, so a batch of the
     // fast lane waits at most a chain's time for SMs, not a whole layer launch's
     if (ok)
@@ -412,14 +414,12 @@ void take_table_job(perm_server_t s, std::vector<Request*>& job) {
     auto& q = s->queues[kLaneTable];
     if (q.empty()) return;
     const int n = q.front()->n;
-    const size_t ws_item = table_bytes(n);
     const size_t avail = arena_largest(s);      // the job's tables are one contiguous range
-    size_t used = 0;
     for (auto it = q.begin(); it != q.end() && (int)job.size() < kTableJob;) {
         Request* r = *it;
         if (r->n != n) { ++it; continue; }
-        if (arena_round(used + ws_item) > avail) break;
-        used += ws_item;
+        const int c = (int)job.size() + 1;
+        if (arena_round(table_bytes(n, c)) > avail) break;
         job.push_back(r);
         it = q.erase(it);
     }
@@ -584,7 +584,7 @@ perm_status perm_submit(perm_server_t s, const void* host_mat, int n, perm_dtype
     // tables fit the budget on the table lane; everything else with Ryser
     int lane;
     if (n <= (dtype == PERM_C128 ? kFastComplexN : kFastIntN)) lane = kLaneFast;
-    else if (auto_uses_sz(dtype) && n <= kMaxNSZ && table_bytes(n) + ((size_t)1 << 20) <= s->table_budget)
+    else if (auto_uses_sz(dtype) && n <= kMaxNSZ && table_bytes_max(n) + ((size_t)1 << 20) <= s->table_budget)
         lane = kLaneTable;
     else lane = kLaneRyser;
     {
