@@ -68,6 +68,8 @@ struct perm_plan_s {
     int layer_grid_small = 2;
     int m_few = 11;               // orders up to kLayerSmallN with at most kLayerFewCount matrices
     bool tail_to_layers = true;   // the batched kernel's last partial round takes the layer path
+    int flow = -1;                // complex orders <= kLayerSmallN, the dataflow layer launch:
+                                  // 1 always, 0 never, -1 for at most kFlowMaxCount matrices
     int c128_threads = 384;       // CTA size of the batched complex kernel
     int int_threads = 256;        // CTA size of the batched integer kernel
     int out_words = 2;            // integer result slot in 64-bit words (4 with PERM_FLAG_WIDE)
@@ -136,6 +138,8 @@ int sz_batch_limit(perm_plan_t p, int complex_cap = 20) {
     if (p->dtype == PERM_C128) best = std::min(best, complex_cap);
     return best;
 }
+
+constexpr int kFlowMaxCount = 4;   // dataflow launch for at most this many matrices of an order
 
 // Chain width of the layer path for order n, with `count` matrices of that order in a launch.
 int layer_m(perm_plan_t p, int n, int count = kLayerFewCount + 1) {
@@ -233,6 +237,7 @@ static perm_status plan_create_core(int n_max, perm_dtype dtype, const perm_opts
         if (sz_int_threads_valid(x)) p->int_threads = x;
     }
     if (const char* v = getenv("LIBPERM_SZ_TAIL_LAYERS")) p->tail_to_layers = atoi(v) != 0;
+    if (const char* v = getenv("LIBPERM_SZ_FLOW")) p->flow = atoi(v) != 0 ? 1 : 0;
     if (const char* v = getenv("LIBPERM_SZ_LAYER_THREADS")) {
         const int x = atoi(v);
         if (x == 384 || x == 512 || x == 768) p->layer_threads = p->layer_threads_small = x;
@@ -492,14 +497,26 @@ perm_status enqueue(perm_plan_t p, const BatchLayout& L, const void* mats, const
             lm = layer_m(p, g.n);
             ws_item = sz_matrix_workspace_bytes(p->dtype, g.n, lm);
         }
+        // complex orders up to kLayerSmallN, a few matrices: every layer in one dataflow launch,
+        // whose chains start as their predecessors finish (measured on GB300: one n = 22 matrix
+        // 0.71 ms against 0.86 ms in layer launches, four 1.62 against 1.80 ms; with 16 or more
+        // matrices the layer launches are already full and the two are within 3 %)
+        const size_t ws_flow = sz_flow_workspace_bytes(g.n, lm);
+        const bool want_flow = p->flow == 1 || (p->flow < 0 && (plain || g.cnt <= kFlowMaxCount));
+        const bool flow = want_flow && small && p->dtype == PERM_C128 && ws_flow <= p->ws_bytes;
+        if (flow) ws_item = ws_flow;
         long long per_launch = ws_item ? (long long)(p->ws_bytes / ws_item) : (long long)g.cnt;
         per_launch = std::max<long long>(1, per_launch);
         if (plain) per_launch = 1;
         for (int b0 = 0; b0 < g.cnt; b0 += (int)per_launch) {
             const int c = (int)std::min<long long>(per_launch, g.cnt - b0);
-            e = sz_launch_layers(p->dtype, mats, dd + g.at + b0, c, g.n, lm, out, p->out_words, item_status,
-                                 p->ws, ws_item, (small ? p->layer_grid_small : p->layer_grid_mult) * p->num_sms,
-                                 st, small ? p->layer_threads_small : p->layer_threads);
+            if (flow)
+                e = sz_launch_flow(mats, dd + g.at + b0, c, g.n, lm, out, item_status, p->ws, ws_item,
+                                   p->d_counter + 1, 2 * p->num_sms, st);
+            else
+                e = sz_launch_layers(p->dtype, mats, dd + g.at + b0, c, g.n, lm, out, p->out_words, item_status,
+                                     p->ws, ws_item, (small ? p->layer_grid_small : p->layer_grid_mult) * p->num_sms,
+                                     st, small ? p->layer_threads_small : p->layer_threads);
             if (e != cudaSuccess) return PERM_ECUDA;
         }
     }

@@ -259,6 +259,18 @@ cudaError_t sz_launch_layers(int dtype, const void* mats, const ItemDesc* items,
                              void* out, int out_words, int* item_status, void* workspace,
                              size_t ws_bytes_per_item, int grid_cap, cudaStream_t st, int threads = 0);
 
+// The layer path of `count` complex matrices of order n <= kLayerSmallN as one
+// persistent dataflow launch (sz_flow_c128): chains start when their
+// predecessors are done instead of at layer boundaries; the same bits as
+// sz_launch_layers.  Matrix c uses [c * ws_bytes_per_item, ...) of the
+// workspace, ws_bytes_per_item >= sz_flow_workspace_bytes(n, m) (three layer
+// regions and the chains' done flags); *counter is zeroed here.  An item whose
+// wait gives up reports PERM_ETIMEDOUT in item_status.
+size_t sz_flow_workspace_bytes(int n, int m);
+cudaError_t sz_launch_flow(const void* mats, const ItemDesc* items, int count, int n, int m, void* out,
+                           int* item_status, void* workspace, size_t ws_bytes_per_item, unsigned* counter,
+                           int grid, cudaStream_t st);
+
 // Ryser: every matrix's codes are cut into ryser_parts(dtype, n) CTA-sized
 // pieces (a function of n only).  One launch per distinct order n.  allow192:
 // integer widths up to 192 bits (requires out_words = 4).  widths: 2 * count

@@ -100,6 +100,7 @@ struct Slot {
     int out_cap = 0;
     ItemDesc* h_desc = nullptr;      // table slots: descriptors of the job's matrices
     ItemDesc* d_desc = nullptr;
+    unsigned* d_counter = nullptr;   // table slots: work counter of a dataflow launch
     size_t ws_off = 0;               // table slots: the job's tables in the arena
     size_t ws_bytes = 0;
     std::vector<Request*> inflight;
@@ -178,6 +179,7 @@ bool slot_alloc(Slot& S, int priority, size_t in_cap, int out_cap, int descs) {
     if (descs > 0) {
         if (cudaMallocHost(&S.h_desc, (size_t)descs * sizeof(ItemDesc)) != cudaSuccess) return false;
         if (cudaMalloc(&S.d_desc, (size_t)descs * sizeof(ItemDesc)) != cudaSuccess) return false;
+        if (cudaMalloc(&S.d_counter, 64) != cudaSuccess) return false;
     }
     return true;
 }
@@ -187,6 +189,7 @@ void slot_free(Slot& S) {
     if (S.d_out) cudaFree(S.d_out);
     if (S.d_status) cudaFree(S.d_status);
     if (S.d_desc) cudaFree(S.d_desc);
+    if (S.d_counter) cudaFree(S.d_counter);
     if (S.h_in) cudaFreeHost(S.h_in);
     if (S.h_out) cudaFreeHost(S.h_out);
     if (S.h_status) cudaFreeHost(S.h_status);
@@ -224,7 +227,13 @@ int table_low(int n, int count) {
     sz_layer_default_shape(n, count, &m, &threads);
     return m;
 }
-size_t table_item_bytes(int n, int count) { return sz_matrix_workspace_bytes(PERM_C128, n, table_low(n, count)); }
+// Jobs of at most this many matrices of an order up to kLayerSmallN run as one dataflow launch.
+constexpr int kTableFlowMax = 4;
+bool table_flow(int n, int count) { return n <= kLayerSmallN && count <= kTableFlowMax; }
+size_t table_item_bytes(int n, int count) {
+    const int m = table_low(n, count);
+    return table_flow(n, count) ? sz_flow_workspace_bytes(n, m) : sz_matrix_workspace_bytes(PERM_C128, n, m);
+}
 size_t table_bytes(int n, int count) { return (size_t)count * table_item_bytes(n, count); }
 // The most one matrix of order n can take (admission to the table lane).
 size_t table_bytes_max(int n) { return std::max(table_item_bytes(n, 1), table_item_bytes(n, kLayerFewCount + 1)); }
@@ -355,9 +364,13 @@ bool table_launch(perm_server_t s, Slot& S, std::vector<Request*>& job) {
                               S.stream) == cudaSuccess;
     int lm = 0, lthreads = 0;
     sz_layer_default_shape(n, c, &lm, &lthreads);
-    // one CTA per chain (no CTA loops over several): CTAs retire every chain, so a batch of the
-    // fast lane waits at most a chain's time for SMs, not a whole layer launch's
-    if (ok)
+    // small jobs: one dataflow launch (a few milliseconds at most); others: one CTA per chain (no
+    // CTA loops over several), so CTAs retire every chain and a batch of the fast lane waits at
+    // most a chain's time for SMs, not a whole layer launch's
+    if (ok && table_flow(n, c))
+        ok = sz_launch_flow(S.d_in, S.d_desc, c, n, lm, S.d_out, S.d_status, ws, ws_item, S.d_counter,
+                            2 * s->num_sms, S.stream) == cudaSuccess;
+    else if (ok)
         ok = sz_launch_layers(PERM_C128, S.d_in, S.d_desc, c, n, lm, S.d_out, 2, S.d_status, ws, ws_item,
                               1 << 30, S.stream, lthreads) == cudaSuccess;
     if (ok) ok = slot_finish_launch(S, (size_t)c * 16, c);

@@ -171,8 +171,16 @@ __device__ __forceinline__ void chain_setup(const MatCtx& mc, unsigned Hmask, in
 // so the accumulation order is all columns ascending.
 // ---------------------------------------------------------------------------
 // COMPACT (orders >= kCompactN): global chains hold the uv plane only, and the outer
-// phase recomputes w = u + v for each predecessor entry it loads.
-template <bool COMPACT>
+// phase recomputes w = u + v for each predecessor entry it loads.  COHERENT: the
+// predecessors are read through L2 only (ld.global.cg), for a kernel in which other
+// CTAs of the same launch wrote them (sz_flow_c128); otherwise through the read-only
+// path.
+template <bool COHERENT>
+__device__ __forceinline__ double2 load_pred2(const double2* p) { return COHERENT ? __ldcg(p) : __ldg(p); }
+template <bool COHERENT>
+__device__ __forceinline__ double load_pred(const double* p) { return COHERENT ? __ldcg(p) : __ldg(p); }
+
+template <bool COMPACT, bool COHERENT = false>
 __device__ void chain_c128(const MatCtx& mc, int s, unsigned char* chain_smem, const double* gprev,
                            double* gdst, const unsigned char* coef_smem, bool last, double2* out,
                            int out_index) {
@@ -205,9 +213,9 @@ __device__ void chain_c128(const MatCtx& mc, int s, unsigned char* chain_smem, c
                 for (int z = 0; z < 4; z++) {
                     if (q + z < s) {
                         const double* pc = gprev + (size_t)hslot[q + z] * cwd;
-                        huv[z] = __ldg(reinterpret_cast<const double2*>(pc) + idx);
+                        huv[z] = load_pred2<COHERENT>(reinterpret_cast<const double2*>(pc) + idx);
                         // compact tables: w = u + v, rounded once, recomputed here
-                        hw[z] = compact ? __fma_rn(huv[z].x, 1.0, huv[z].y) : __ldg(pc + 2 * CL + idx);
+                        hw[z] = compact ? __fma_rn(huv[z].x, 1.0, huv[z].y) : load_pred<COHERENT>(pc + 2 * CL + idx);
                     }
                 }
 #pragma unroll
@@ -249,7 +257,7 @@ __device__ void chain_c128(const MatCtx& mc, int s, unsigned char* chain_smem, c
                 const double2* fxy = cxy + (n - 1) * n;
                 dd2 re = {0.0, 0.0}, im = {0.0, 0.0};
                 for (int q = 0; q < s; q++) {
-                    const double2 p = reinterpret_cast<const double2*>(gprev + (size_t)hslot[q] * cwd)[idx];
+                    const double2 p = load_pred2<COHERENT>(reinterpret_cast<const double2*>(gprev + (size_t)hslot[q] * cwd) + idx);
                     const double2 c = fxy[hcol[q]];
                     re = dd_add_prod(re, c.x, p.x);
                     re = dd_add_prod(re, -c.y, p.y);
@@ -478,14 +486,14 @@ __host__ __device__ inline size_t chain_words(int kind, int m, bool compact = fa
     return (size_t)(kind == kC128 ? (compact ? 2 : 3) : (kind == kU64 ? 1 : 2)) << m;
 }
 
-// One chain of a matrix, any element kind (COMPACT: complex compact tables).
-template <int KIND, bool ZO, bool COMPACT = false>
+// One chain of a matrix, any element kind (COMPACT, COHERENT: see chain_c128).
+template <int KIND, bool ZO, bool COMPACT = false, bool COHERENT = false>
 __device__ __forceinline__ void run_chain(const MatCtx& mc, int s, unsigned char* smem_chain,
                                           const unsigned long long* src, unsigned long long* dst,
                                           const unsigned char* coef, bool last, void* out,
                                           int out_index) {
     if (KIND == kC128)
-        chain_c128<COMPACT>(mc, s, smem_chain, reinterpret_cast<const double*>(src),
+        chain_c128<COMPACT, COHERENT>(mc, s, smem_chain, reinterpret_cast<const double*>(src),
                    reinterpret_cast<double*>(dst), coef, last, reinterpret_cast<double2*>(out),
                    out_index);
     else
@@ -630,6 +638,126 @@ sz_layer_c128(const double2* __restrict__ mats, const ItemDesc* __restrict__ ite
                                          last ? nullptr : dst_region + (size_t)slot * CW, smem + L.coef_off,
                                          last, out, d.out_index);
         if (last && threadIdx.x == 0 && item_status) item_status[d.out_index] = PERM_OK;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Dataflow form of the layer path (complex, orders up to kLayerSmallN): one
+// persistent launch runs every layer of `count` matrices of order n.  Work
+// items are (layer s, matrix c, chain slot), numbered in that order and taken
+// from an atomic counter.  An item starts once the s predecessor chains it
+// reads are done (a flag per chain) and every chain of layer s - 2 is done (a
+// counter per layer): three layer regions rotate, and region s mod 3 held layer
+// s - 3, which only layer s - 2 reads.  So the first chains of a layer overlap
+// the last chains of the one before instead of waiting for a whole launch.
+// Every item's dependencies have smaller numbers, so they were taken before by
+// CTAs that are running: every wait ends.  Each wait is still bounded (about a
+// second of clock), after which the chain is skipped, still marked done, and
+// its matrix reports PERM_ETIMEDOUT.
+//
+// Per matrix the workspace holds the three regions, then one done flag per chain
+// of every layer (layer s's at offset sum_{s' < s} C(t, s')), the done counters of
+// layers 0..t, and an error flag; all of them zero at launch.
+// ---------------------------------------------------------------------------
+constexpr int kThreadsFlow = 384;
+constexpr long long kFlowWaitCycles = 2000000000ll;   // about one second at the GB300's clock
+
+__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_gpu(int* p, int v) {
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Spin until *p >= need, at most until `start + kFlowWaitCycles`; false on time-out.
+__device__ inline bool flow_wait(const int* p, int need, long long start) {
+    while (ld_acquire_gpu(p) < need) {
+        if (clock64() - start > kFlowWaitCycles) return false;
+        __nanosleep(128);
+    }
+    return true;
+}
+
+__host__ __device__ inline size_t flow_layer_words(int n, int m) {
+    const int t = n - m;
+    return (size_t)binom_calc(t, t / 2) * chain_words(kC128, m);
+}
+
+__global__ void __launch_bounds__(kThreadsFlow, 2)
+sz_flow_c128(const double2* __restrict__ mats, const ItemDesc* __restrict__ items, int count, int n,
+             int m_param, double2* out, int* item_status, unsigned long long* workspace,
+             size_t ws_words_per_item, unsigned* counter) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ unsigned s_item;
+    __shared__ int s_ok;
+    fill_binom(reinterpret_cast<unsigned*>(smem));
+    const SmemLayout L = smem_layout(kC128, n, sz_low_for(n, m_param));
+    MatCtx mc;
+    init_ctx(mc, n, m_param, smem, L);
+    const int t = mc.t;
+    const size_t CW = chain_words(kC128, mc.m);
+    const size_t layer_words = flow_layer_words(n, mc.m);
+    const unsigned chains = 1u << t;                   // chains of one matrix, all layers
+    const unsigned total = (unsigned)count * chains;
+    int* hinfo = reinterpret_cast<int*>(smem + L.hinfo_off);
+    int cur = -1;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1u);
+        __syncthreads();
+        const unsigned i = s_item;
+        if (i >= total) break;
+        // (layer, matrix, slot) of item i; fb = the layer's first flag in a matrix
+        int s = 0;
+        unsigned base = 0, fb = 0;
+        while (base + (unsigned)count * mc.bn[t * (kBinomDim + 1) + s] <= i) {
+            const unsigned cs = mc.bn[t * (kBinomDim + 1) + s];
+            base += (unsigned)count * cs;
+            fb += cs;
+            s++;
+        }
+        const unsigned nslots = mc.bn[t * (kBinomDim + 1) + s];
+        const int c = (int)((i - base) / nslots);
+        const unsigned slot = (i - base) % nslots;
+        const ItemDesc d = items[c];
+        unsigned long long* ws = workspace + (size_t)c * ws_words_per_item;
+        int* flags = reinterpret_cast<int*>(ws + 3 * layer_words);
+        int* done = flags + chains;                        // layers 0..t
+        int* err = done + t + 1;
+        chain_setup(mc, unrank_high(slot, s, t, mc.bn), hinfo);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const long long start = clock64();
+            bool ok = true;
+            const unsigned pfb = fb - (s >= 1 ? mc.bn[t * (kBinomDim + 1) + s - 1] : 0u);
+            for (int q = 0; q < s && ok; q++) ok = flow_wait(flags + pfb + hinfo[q], 1, start);
+            if (ok && s >= 2) ok = flow_wait(done + s - 2, (int)mc.bn[t * (kBinomDim + 1) + s - 2], start);
+            if (!ok) atomicExch(err, 1);
+            s_ok = ok;
+        }
+        if (c != cur) {                                    // the same for the whole CTA
+            load_coef_c128(mats + d.offset, n, smem + L.coef_off);
+            cur = c;
+        }
+        __syncthreads();
+        const bool last = (s == t);
+        unsigned long long* dst = ws + (size_t)(s % 3) * layer_words + (size_t)slot * CW;
+        const unsigned long long* src = ws + (size_t)((s + 2) % 3) * layer_words;
+        if (s_ok) {
+            run_chain<kC128, false, false, true>(mc, s, smem + L.chain_off, src, last ? nullptr : dst,
+                                                 smem + L.coef_off, last, out, d.out_index);
+        }
+        // the chain's entries visible to every SM, then its flag and its layer's count
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            atomicAdd(done + s, 1);
+            st_release_gpu(flags + fb + slot, 1);
+            if (last && item_status)
+                item_status[d.out_index] = ld_acquire_gpu(err) ? PERM_ETIMEDOUT : PERM_OK;
+        }
     }
 }
 
@@ -916,6 +1044,34 @@ cudaError_t sz_launch_layers_impl(int dtype, const void* mats, const ItemDesc* i
 
 }  // namespace
 
+size_t sz_flow_workspace_bytes(int n, int m_param) {
+    const int m = sz_low_for(n, m_param);
+    const int t = n - m;
+    const size_t bytes = 3 * flow_layer_words(n, m) * 8 + (((size_t)1 << t) + t + 2) * sizeof(int);
+    return (bytes + 255) & ~(size_t)255;
+}
+
+cudaError_t sz_launch_flow(const void* mats, const ItemDesc* items, int count, int n, int m, void* out,
+                           int* item_status, void* workspace, size_t ws_bytes_per_item, unsigned* counter,
+                           int grid, cudaStream_t st) {
+    if (count <= 0) return cudaSuccess;
+    if (n > kLayerSmallN || ws_bytes_per_item < sz_flow_workspace_bytes(n, m)) return cudaErrorInvalidValue;
+    const int mm = sz_low_for(n, m);
+    const int t = n - mm;
+    const size_t flag_off = 3 * flow_layer_words(n, mm) * 8;
+    const size_t flag_bytes = (((size_t)1 << t) + t + 2) * sizeof(int);
+    cudaError_t e = cudaMemset2DAsync(static_cast<unsigned char*>(workspace) + flag_off, ws_bytes_per_item, 0,
+                                      flag_bytes, (size_t)count, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(unsigned), st);
+    const int smem = sz_smem_bytes(PERM_C128, n, m);
+    if (e == cudaSuccess) e = set_smem((const void*)sz_flow_c128, smem);
+    if (e != cudaSuccess) return e;
+    sz_flow_c128<<<grid, kThreadsFlow, smem, st>>>((const double2*)mats, items, count, n, m, (double2*)out,
+                                                   item_status, (unsigned long long*)workspace,
+                                                   ws_bytes_per_item / 8, counter);
+    return cudaGetLastError();
+}
+
 cudaError_t sz_launch_layers(int dtype, const void* mats, const ItemDesc* items, int count, int n, int m,
                              void* out, int out_words, int* item_status, void* workspace,
                              size_t ws_bytes_per_item, int grid_cap, cudaStream_t st, int threads) {
@@ -932,7 +1088,7 @@ cudaError_t sz_launch_single(int dtype, const void* mats, long long offset, int 
 
 cudaError_t sz_preload(int dtype) {
     cudaFuncAttributes fa;
-    const void* fns[12];
+    const void* fns[14];
     int k = 0;
     fns[k++] = (const void*)trivial_kernel;
     if (dtype == PERM_C128) {
@@ -942,6 +1098,7 @@ cudaError_t sz_preload(int dtype) {
         fns[k++] = c128_batched_fn(768);
         for (int threads : {384, 512, 768})
             for (bool compact : {false, true}) fns[k++] = (const void*)pick_c128_layer(threads, compact);
+        fns[k++] = (const void*)sz_flow_c128;
     } else {
         for (int n_max : {20, 34})
             for (int threads : {256, 512}) fns[k++] = (const void*)pick_int_batched(dtype, n_max, threads);
