@@ -322,8 +322,8 @@ def run_gpu(args, rank, world):
     # (Ryser: width, Gray-code and finishing kernels; --int-method sz: one batched kernel)
     dc = pc.describe()
     tail = count % dc["batched_grid"] if count > dc["batched_grid"] else 0
-    launches_per_step = 1 + ((N - dc["chain_width_single"] + 1) if tail else 0) + \
-        (1 if args.int_method == "sz" else 3)
+    tail_m = dc["chain_width_layer_small"] if N <= dc["layer_small_nmax"] else dc["chain_width_single"]
+    launches_per_step = 1 + ((N - tail_m + 1) if tail else 0) + (1 if args.int_method == "sz" else 3)
     # achieved: the method's own work per permanent (n(2^(n-1)-1) complex multiplications at
     # 6 flops, (n-2)2^(n-1)+1 complex additions at 2), the per-unit figure of the roofline
     flops = sz_c128_standard_flops(N) * count
@@ -393,7 +393,7 @@ def measure_extras(lp, torch, cm, im, stream, c_kernel_ms, count):
         "batched_complex_perm_per_s": count / (c_kernel_ms / 1000.0),
         "speedup": (count / c_kernel_ms) / (sample / plain_ms),
         "plain_sample": sample,
-        "plain": "one matrix at a time, Store-zechin chain layers over the whole GPU (chains of 2^11: 10 launches per matrix)"}
+        "plain": "one matrix at a time over the whole GPU (Store-zechin chains of 2^11, one dataflow launch per matrix)"}
     # single n = 32 instance, both kernels
     from paper_1802_02779_gb300 import workloads as wl
     a32 = wl.single_n32()
