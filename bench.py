@@ -117,10 +117,10 @@ class Clocks:
 
 
 # DRAM bytes (read + write) per n = 20 complex matrix of sz_batched_c128, from the ncu capture
-# summarised in profiles/sz_batched_c128_n20.md (304 matrices: 29.750551 GB + 7.623576 GB).
+# summarised in profiles/sz_batched_c128_n20.md (304 matrices: 29.764249 GB + 7.642200 GB).
 # Valid only for the kernel source it was measured on; otherwise the bench reports null.
-TRAFFIC_C128_PER_MATRIX = (29.750551e9 + 7.623576e9) / 304
-TRAFFIC_SOURCE_SHA256 = "7dd7e272a530ec5e99e854805fad8a8172d653487622195d8ece34b9941bff6e"
+TRAFFIC_C128_PER_MATRIX = (29.764249e9 + 7.642200e9) / 304
+TRAFFIC_SOURCE_SHA256 = "9e0763c5d4defb0c3b5110cc5e59b8ce847b4763b0e8f81d4e2f2732fe5ad717"
 
 
 def traffic_per_launch(count: int):
