@@ -597,6 +597,241 @@ sz_batched_int(const long long* __restrict__ mats, const ItemDesc* __restrict__ 
 }
 
 // ---------------------------------------------------------------------------
+// 0/1 matrices modulo 2^64 (every 0/1 matrix of order <= 20: 20! < 2^64) with
+// register rows.  The 2^m entries of a chain are grouped into rows of 2^RB
+// entries that differ only in the RB lowest chain columns ("lo"); the other
+// h = m - RB chain columns ("hi") name the row.
+//
+// Phase 1 (outer terms) is chain_int's, two entries per thread and load.
+// Phase 2 walks the rows in h + 1 stages by popcount(hi), one barrier per
+// stage: a thread takes a row, adds for every hi column i of the row the row
+// hi \ i (finished in an earlier stage, read from shared memory), then the
+// terms inside the row in registers, in increasing lo, so that every entry
+// it reads is complete.  Each entry sums exactly the terms of the §4
+// recurrence, T[S] = sum over j in S with a[|S|-1][j] = 1 of T[S \ j]; only
+// the order of the additions differs from chain_int, which modulo 2^64
+// changes nothing.
+//
+// Shared memory: E, 2^m u64 by row, row hi as 2^(RB-1) 16-byte pairs, pair z
+// stored at z ^ swz(hi) so that the rows a quarter warp reads together fall
+// on different banks.  Global chain: natural order of the chain mask
+// c = hi * 2^RB + lo.
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int popc_const(int x) { return x ? (x & 1) + popc_const(x >> 1) : 0; }
+
+template <int RB>
+__device__ __forceinline__ unsigned zo_pair(unsigned hi, unsigned z) {
+    constexpr unsigned kPairs = 1u << (RB - 1);
+    return hi * kPairs + (z ^ ((hi >> (4 - RB)) & (kPairs - 1)));
+}
+
+// Per chain H (s outer columns, every thread passes the same H): pslot[p], the
+// slot of H minus its p-th column among the (s-1)-subsets (colex rank), and
+// obits[k] for k = s..s+m, bit p set when a[k-1][p-th column of H] != 0.
+__device__ __forceinline__ void zo_chain_setup(const MatCtx& mc, const unsigned long long* coef,
+                                               unsigned H, int s, int* pslot, unsigned* obits) {
+    const unsigned* bn = mc.bn;
+    const int x = (int)threadIdx.x;
+    if (x < s) {
+        unsigned slot = 0;
+        int q = 0;
+        for (unsigned hm = H; hm; hm &= hm - 1, q++) {
+            const int b = __ffs(hm) - 1;
+            if (q < x) slot += bn[b * (kBinomDim + 1) + q + 1];
+            else if (q > x) slot += bn[b * (kBinomDim + 1) + q];
+        }
+        pslot[x] = (int)slot;
+    } else if (x >= 32 && x - 32 <= mc.m) {
+        const int k = s + (x - 32);
+        unsigned bits = 0;
+        if (k >= 1) {
+            int p = 0;
+            for (unsigned hm = H; hm; hm &= hm - 1, p++)
+                if (coef[(size_t)(k - 1) * mc.n + (__ffs(hm) - 1)] != 0ull) bits |= 1u << p;
+        }
+        obits[k] = bits;
+    }
+}
+
+template <int RB>
+__device__ void chain_zo64(const MatCtx& mc, int s, ulonglong2* E, const unsigned long long* gprev,
+                           unsigned long long* gdst, const int* pslot, const unsigned* obits,
+                           bool last, unsigned long long* out, int out_index) {
+    constexpr int kRow = 1 << RB, kPairs = kRow / 2;
+    const int m = mc.m, h = m - RB;
+    const unsigned CL = 1u << m;
+
+    // ---- phase 1: outer terms, entries c and c + 1 (c even) per thread ----
+    if (s >= 1) {
+        unsigned po[8];                          // first eight predecessor chains (a layer region
+#pragma unroll                                   // of at most 2^19 words for orders <= 20)
+        for (int z = 0; z < 8; z++) po[z] = (unsigned)pslot[z < s ? z : 0] * CL;
+        for (unsigned e = threadIdx.x; e < CL / 2; e += blockDim.x) {
+            const unsigned c = 2 * e;
+            const int k = s + __popc(c);
+            const unsigned ob0 = obits[k], ob1 = obits[k + 1];
+            const unsigned ob = ob0 | ob1;
+            unsigned long long a0 = 0ull, a1 = 0ull;
+#pragma unroll
+            for (int z0 = 0; z0 < 8; z0 += 4) {
+                if (z0 < s) {
+                    ulonglong2 v[4];
+#pragma unroll
+                    for (int z = 0; z < 4; z++) {
+                        v[z] = make_ulonglong2(0ull, 0ull);
+                        if ((ob >> (z0 + z)) & 1u)
+                            v[z] = __ldg(reinterpret_cast<const ulonglong2*>(gprev + po[z0 + z] + c));
+                    }
+#pragma unroll
+                    for (int z = 0; z < 4; z++) {
+                        if ((ob0 >> (z0 + z)) & 1u) a0 += v[z].x;
+                        if ((ob1 >> (z0 + z)) & 1u) a1 += v[z].y;
+                    }
+                }
+            }
+            for (int p = 8; p < s; p++) {        // more than eight outer columns
+                if ((ob >> p) & 1u) {
+                    const ulonglong2 w =
+                        __ldg(reinterpret_cast<const ulonglong2*>(gprev + (size_t)pslot[p] * CL + c));
+                    if ((ob0 >> p) & 1u) a0 += w.x;
+                    if ((ob1 >> p) & 1u) a1 += w.y;
+                }
+            }
+            E[zo_pair<RB>(c >> RB, (c & (kRow - 1)) >> 1)] = make_ulonglong2(a0, a1);
+        }
+        __syncthreads();
+    }
+
+    // ---- phase 2: rows by popcount(hi) ----
+    const unsigned short* rows = g_masks + ((1u << h) - 2);
+    const unsigned full = (1u << h) - 1;
+    unsigned off = 0;
+    for (int q = 0; q <= h; q++) {
+        const unsigned cnt = mc.bn[h * (kBinomDim + 1) + q];
+        const int kr = s + q;                    // level of the row's entry lo = 0
+        unsigned R[RB + 1];
+        unsigned any = 0;
+#pragma unroll
+        for (int p = 0; p <= RB; p++) {
+            R[p] = (kr + p >= 1) ? mc.rowmask[kr + p - 1] : 0u;
+            any |= R[p];
+        }
+        any >>= RB;
+        for (unsigned rr = threadIdx.x; rr < cnt; rr += blockDim.x) {
+            const unsigned hi = rows[off + rr];
+            unsigned long long v[kRow];
+            if (s >= 1) {
+#pragma unroll
+                for (int z = 0; z < kPairs; z++) {
+                    const ulonglong2 x = E[zo_pair<RB>(hi, z)];
+                    v[2 * z] = x.x;
+                    v[2 * z + 1] = x.y;
+                }
+            } else {
+#pragma unroll
+                for (int lo = 0; lo < kRow; lo++) v[lo] = 0ull;
+                if (hi == 0) v[0] = 1ull;          // T[empty set] = 1
+            }
+            // rows hi \ i
+            unsigned mm = hi & any;
+            while (mm) {
+                const int i = __ffs(mm) - 1;
+                mm &= mm - 1;
+                const unsigned nb = hi ^ (1u << i);
+                unsigned long long w[kRow];
+#pragma unroll
+                for (int z = 0; z < kPairs; z++) {
+                    const ulonglong2 x = E[zo_pair<RB>(nb, z)];
+                    w[2 * z] = x.x;
+                    w[2 * z + 1] = x.y;
+                }
+#pragma unroll
+                for (int lo = 0; lo < kRow; lo++)
+                    if ((R[popc_const(lo)] >> (RB + i)) & 1u) v[lo] += w[lo];
+            }
+            // terms inside the row, in increasing lo
+#pragma unroll
+            for (int lo = 1; lo < kRow; lo++)
+#pragma unroll
+                for (int b = 0; b < RB; b++)
+                    if (((lo >> b) & 1) && ((R[popc_const(lo)] >> b) & 1u)) v[lo] += v[lo ^ (1 << b)];
+#pragma unroll
+            for (int z = 0; z < kPairs; z++) {
+                const ulonglong2 x = make_ulonglong2(v[2 * z], v[2 * z + 1]);
+                E[zo_pair<RB>(hi, z)] = x;
+                if (gdst) reinterpret_cast<ulonglong2*>(gdst)[(size_t)hi * kPairs + z] = x;
+            }
+            if (last && hi == full) {
+                unsigned long long* dst = out + (size_t)mc.out_words * out_index;
+                dst[0] = v[kRow - 1];
+                dst[1] = 0ull;
+                if (mc.out_words == 4) { dst[2] = 0ull; dst[3] = 0ull; }
+            }
+        }
+        off += cnt;
+        __syncthreads();
+    }
+}
+
+// Batched 0/1 kernel for orders <= 20 with the register-row chains (chains
+// narrower than RB + 1 columns take chain_int).  Same arguments and results as
+// sz_batched_int<true, true, THREADS>; the chain tables in the workspace are
+// in natural mask order instead of the mask-list order.
+template <int THREADS, int RB>
+__global__ void __launch_bounds__(THREADS, THREADS == 256 ? 5 : 2)
+sz_batched_zo64(const long long* __restrict__ mats, const ItemDesc* __restrict__ items, int count,
+                int m_param, unsigned long long* out, int out_words, int* item_status,
+                unsigned long long* workspace, size_t ws_words_per_cta, unsigned* counter) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_item;
+    __shared__ int s_width;
+    __shared__ int s_pslot[kBinomDim];
+    __shared__ unsigned s_obits[kMaxN + 2];
+    fill_binom(reinterpret_cast<unsigned*>(smem));
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(counter, 1u);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= count) break;
+        const ItemDesc d = items[it];
+        const int n = d.n;
+        if (threadIdx.x == 0) s_width = decide_width(mats + d.offset, n, true);
+        const SmemLayout L = smem_layout(kU64, n, sz_low_for(n, m_param));
+        MatCtx mc;
+        init_ctx(mc, n, m_param, smem, L);
+        mc.out_words = out_words;
+        unsigned long long* coef = reinterpret_cast<unsigned long long*>(smem + L.coef_off);
+        load_coef_int(mats + d.offset, n, mc.m, coef, reinterpret_cast<unsigned*>(smem + L.rowmask_off));
+        __syncthreads();
+        const int w = s_width;
+        unsigned long long* ws = workspace + (size_t)blockIdx.x * ws_words_per_cta;
+        if (mc.m < RB + 1) {
+            run_matrix_cta<kU64, true>(mc, smem + L.chain_off, ws, smem + L.coef_off, out, d.out_index,
+                                       reinterpret_cast<int*>(smem + L.hinfo_off));
+        } else {
+            const size_t CW = chain_words(kU64, mc.m);
+            const size_t layer_words = (size_t)binom_calc(mc.t, mc.t / 2) * CW;
+            ulonglong2* E = reinterpret_cast<ulonglong2*>(smem + L.chain_off);
+            for (int s = 0; s <= mc.t; s++) {
+                const unsigned nslots = (unsigned)binom_calc(mc.t, s);
+                unsigned long long* dst_region = ws + (size_t)(s & 1) * layer_words;
+                const unsigned long long* src_region = ws + (size_t)((s + 1) & 1) * layer_words;
+                const bool last = (s == mc.t);
+                for (unsigned slot = 0; slot < nslots; slot++) {
+                    zo_chain_setup(mc, coef, unrank_high(slot, s, mc.t, mc.bn), s, s_pslot, s_obits);
+                    __syncthreads();
+                    chain_zo64<RB>(mc, s, E, src_region, last ? nullptr : dst_region + (size_t)slot * CW,
+                                   s_pslot, s_obits, last, out, d.out_index);
+                    // every chain ends with __syncthreads()
+                }
+            }
+        }
+        if (item_status && threadIdx.x == 0) item_status[d.out_index] = width_status(w);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // One-matrix-at-a-time path, several matrices of one order per launch: one
 // launch per layer s, the CTAs stride over the (matrix, chain slot) pairs of
 // that layer.  Matrix c of the launch keeps its two layer regions at
@@ -829,10 +1064,22 @@ __global__ void trivial_kernel(int dtype, const ItemDesc* items, int count, void
 typedef void (*int_batched_fn)(const long long*, const ItemDesc*, int, int, unsigned long long*, int,
                                int*, unsigned long long*, size_t, unsigned*);
 
+// 0/1 batches of order <= 20 take the register-row chains (rows of 2^2
+// entries); the LIBPERM_SZ_ZO_ROW=0 experiment knob keeps them on the
+// mask-list chains of sz_batched_int.  Same results either way.
+bool zo_register_rows() {
+    static const bool on = [] {
+        const char* v = getenv("LIBPERM_SZ_ZO_ROW");
+        return !(v && atoi(v) == 0);
+    }();
+    return on;
+}
+
 template <int T>
 int_batched_fn pick_int_batched_t(int dtype, int n_max) {
     const bool zo = dtype == PERM_U01;
-    if (zo && n_max <= 20) return sz_batched_int<true, true, T>;     // 20! < 2^64
+    if (zo && n_max <= 20)                                            // 20! < 2^64
+        return zo_register_rows() ? sz_batched_zo64<T, 2> : sz_batched_int<true, true, T>;
     if (zo) return sz_batched_int<true, false, T>;
     return sz_batched_int<false, false, T>;
 }
