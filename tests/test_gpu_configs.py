@@ -199,3 +199,21 @@ def test_store_zechin_n34_in_hbm(lp):
     want_r1 = math.factorial(n) * np.prod(x) * np.prod(y)
     scale_r1 = math.factorial(n) * np.prod(np.abs(x)) * np.prod(np.abs(y))
     assert abs(got[1] - want_r1) <= 1e-12 * scale_r1, (got[1], want_r1)
+
+
+@pytest.mark.parametrize("method", ["sz", "ryser"])
+def test_compact_orders_general_matrices(lp, method):
+    """General complex matrices of order 33 (and 34) from the serving stream -- the orders
+    with compact Store-zechin tables -- against the oracle's stored double-double values
+    (tests/golden/make_compact_orders.py)."""
+    gold = _golden("compact_orders.json")
+    reqs = wl.uneven_requests(**gold["stream"])
+    assert gold["cases"] and gold["cases"][0]["n"] == 33
+    m = lp.METHOD_SZ if method == "sz" else lp.METHOD_RYSER
+    for c in gold["cases"]:
+        a = reqs[c["index"]].mat
+        assert a.shape == (c["n"], c["n"]) and reqs[c["index"]].dtype == "c128"
+        with lp.Plan(c["n"], "c128", method=m, max_batch=1, mem_budget_bytes=100 << 30) as p:
+            got = lp.permanents([a], "c128", plan=p)[0]
+        want = complex(*c["per"])
+        assert abs(got - want) <= 1e-12 * c["per_abs"], (c["n"], method, got, want)
