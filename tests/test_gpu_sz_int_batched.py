@@ -2,8 +2,9 @@
 
 A call takes the batched kernel only when it holds at least as many
 Store-zechin matrices as the GPU has SMs, so every call here repeats a set of
-matrices to fill it.  Covered: 0/1 matrices of order <= 20 (64-bit chains
-only), 0/1 matrices of order 21..23 (64- and 128-bit chains chosen per
+matrices to fill it.  Covered: 0/1 matrices of order <= 20 (the register-row
+kernel, 64-bit chains; orders 1 and 2 and chain widths below 3 on the mask-list
+chains), 0/1 matrices of order 21..23 (64- and 128-bit chains chosen per
 matrix), small nonnegative integers (multiply-add, 64 and 128 bits), chain
 widths 3..13 (fewer than five low columns: partial warp tasks; 13: two passes
 of the outer phase) and CTAs of 256 and 512 threads.  Every value is exact."""
@@ -66,6 +67,36 @@ def test_01_closed_forms_and_128_bits(lp):
     mats.append(rand01(22, 12100, p=0.5))
     want.append(oracle_i(mats[-1]))
     assert _run(lp, mats, "u01") == want
+
+
+@pytest.mark.parametrize("low_cols", [0, 3, 12, 13])
+def test_01_register_rows_closed_forms(lp, low_cols):
+    """0/1 batches of order <= 20 (the register-row kernel) on matrices with closed forms:
+    J_n = n!, J - I = D_n, a zero row or column = 0, a permutation matrix = 1, an upper
+    triangular matrix of ones = 1, and a block-diagonal matrix = the product of its blocks."""
+    mats, want = [], []
+    d = [1, 0]
+    for k in range(2, 21):
+        d.append((k - 1) * (d[-1] + d[-2]))
+    for n in (3, 7, 13, 19, 20):
+        J = np.ones((n, n), dtype=np.int64)
+        mats += [J, J - np.eye(n, dtype=np.int64)]
+        want += [math.factorial(n), d[n]]
+    z = rand01(18, 12400, p=0.6)
+    z[11, :] = 0
+    mats.append(z); want.append(0)
+    z = rand01(20, 12401, p=0.6)
+    z[:, 19] = 0
+    mats.append(z); want.append(0)
+    perm = np.random.default_rng(12402).permutation(20)
+    mats.append(np.eye(20, dtype=np.int64)[perm]); want.append(1)
+    mats.append(np.triu(np.ones((20, 20), dtype=np.int64))); want.append(1)
+    b1, b2 = rand01(9, 12403, p=0.5), rand01(11, 12404, p=0.5)
+    blk = np.zeros((20, 20), dtype=np.int64)
+    blk[:9, :9] = b1
+    blk[9:, 9:] = b2
+    mats.append(blk); want.append(oracle_i(b1) * oracle_i(b2))
+    assert _run(lp, mats, "u01", low_cols=low_cols) == want
 
 
 @pytest.mark.parametrize("low_cols", [0, 4, 12])
