@@ -117,10 +117,10 @@ class Clocks:
 
 
 # DRAM bytes (read + write) per n = 20 complex matrix of sz_batched_c128, from the ncu capture
-# summarised in profiles/sz_batched_c128_n20.md (304 matrices: 29.764249 GB + 7.642200 GB).
+# summarised in profiles/sz_batched_c128_n20.md (304 matrices: 29.766831 GB + 7.642462 GB).
 # Valid only for the kernel source it was measured on; otherwise the bench reports null.
-TRAFFIC_C128_PER_MATRIX = (29.764249e9 + 7.642200e9) / 304
-TRAFFIC_SOURCE_SHA256 = "9e0763c5d4defb0c3b5110cc5e59b8ce847b4763b0e8f81d4e2f2732fe5ad717"
+TRAFFIC_C128_PER_MATRIX = (29.766831e9 + 7.642462e9) / 304
+TRAFFIC_SOURCE_SHA256 = "11c65476b0e1da6e35a45fe97a37085eb8f14fe79c84b21fd0fed650b227bfe5"
 
 
 def traffic_per_launch(count: int):
@@ -350,13 +350,15 @@ def run_gpu(args, rank, world):
            "sample": f"{dc} complex + {di} 0/1 matrices of the workload in {dt:.1f} s "
                      f"(double-double / exact Ryser Eq. (4), OpenMP)"}
 
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+    metric = METRIC if args.int_method != "sz" else METRIC.replace("by the integer default, Ryser",
+                                                                   "by Store-zechin (--int-method sz)")
+    line = {"metric": metric, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64+u64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": N, "complex128": count, "zero_one": count,
                        "method": {"complex128": "Store-zechin, persistent batched launch (one CTA per matrix)",
-                                  "zero_one": ("Store-zechin batched integer kernel (--int-method sz)"
+                                  "zero_one": ("Store-zechin batched 0/1 kernel, register rows (--int-method sz)"
                                                if args.int_method == "sz" else
                                                "Ryser Gray-code kernel (PERM_METHOD_AUTO's method for integers): "
                                                "width kernel, one CTA per 2^16 Glynn codes, finishing kernel")},
