@@ -382,6 +382,7 @@ def measure_extras(lp, torch, cm, im, stream, c_kernel_ms, count):
     c_dev = torch.from_numpy(np.ascontiguousarray(cm[:sample]).reshape(-1)).cuda()
     o = torch.empty(sample, dtype=torch.complex128, device="cuda")
     with lp.Plan(N, "c128", flags=lp.FLAG_PLAIN, max_batch=sample) as pp:
+        few_m = pp.describe()["chain_width_layer_few_n20"]
         pp.batch(c_dev, [N] * sample, o, None, stream)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -395,7 +396,8 @@ def measure_extras(lp, torch, cm, im, stream, c_kernel_ms, count):
         "batched_complex_perm_per_s": count / (c_kernel_ms / 1000.0),
         "speedup": (count / c_kernel_ms) / (sample / plain_ms),
         "plain_sample": sample,
-        "plain": "one matrix at a time over the whole GPU (Store-zechin chains of 2^11, one dataflow launch per matrix)"}
+        "plain": f"one matrix at a time over the whole GPU (Store-zechin chains of 2^{few_m}, one dataflow "
+                 "launch per matrix)"}
     # single n = 32 instance, both kernels
     from paper_1802_02779_gb300 import workloads as wl
     a32 = wl.single_n32()

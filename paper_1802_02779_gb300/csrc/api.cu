@@ -66,7 +66,8 @@ struct perm_plan_s {
     int m_small = 12;
     int layer_threads_small = 384;
     int layer_grid_small = 2;
-    int m_few = 11;               // orders up to kLayerSmallN with at most kLayerFewCount matrices
+    int m_few = 0;                // orders up to kLayerSmallN, at most kFlowMaxCount matrices:
+                                  // 0 = by order and count (sz_layer_default_shape), else this
     bool tail_to_layers = true;   // the batched kernel's last partial round takes the layer path
     int flow = -1;                // complex orders <= kLayerSmallN, the dataflow layer launch:
                                   // 1 always, 0 never, -1 for at most kFlowMaxCount matrices
@@ -139,12 +140,15 @@ int sz_batch_limit(perm_plan_t p, int complex_cap = 20) {
     return best;
 }
 
-constexpr int kFlowMaxCount = 4;   // dataflow launch for at most this many matrices of an order
-
-// Chain width of the layer path for order n, with `count` matrices of that order in a launch.
-int layer_m(perm_plan_t p, int n, int count = kLayerFewCount + 1) {
+// Chain width of the layer path for order n, with `count` matrices of that order in a launch
+// (the default: more than kFlowMaxCount).
+int layer_m(perm_plan_t p, int n, int count = kFlowMaxCount + 1) {
     if (n > kLayerSmallN) return p->m_single;
-    return count <= kLayerFewCount ? p->m_few : p->m_small;
+    if (count > kFlowMaxCount || p->dtype != PERM_C128) return p->m_small;
+    if (p->m_few) return p->m_few;
+    int m = 0, threads = 0;
+    sz_layer_default_shape(n, count, &m, &threads);
+    return m;
 }
 
 }  // namespace
@@ -219,11 +223,9 @@ static perm_status plan_create_core(int n_max, perm_dtype dtype, const perm_opts
     p->out_words = (o.flags & PERM_FLAG_WIDE) ? 4 : 2;
     p->max_batch = o.max_batch ? o.max_batch : 65536;
     p->m_low = o.low_cols ? o.low_cols : 12;
-    int few_threads = 0;
-    sz_layer_default_shape(kLayerSmallN + 1, kLayerFewCount + 1, &p->m_single, &p->layer_threads);
-    sz_layer_default_shape(kLayerSmallN, kLayerFewCount + 1, &p->m_small, &p->layer_threads_small);
-    sz_layer_default_shape(kLayerSmallN, 1, &p->m_few, &few_threads);
-    if (dtype != PERM_C128) p->m_small = p->m_few = p->m_single;   // integers: one shape (the 256-thread kernel)
+    sz_layer_default_shape(kLayerSmallN + 1, kFlowMaxCount + 1, &p->m_single, &p->layer_threads);
+    sz_layer_default_shape(kLayerSmallN, kFlowMaxCount + 1, &p->m_small, &p->layer_threads_small);
+    if (dtype != PERM_C128) p->m_small = p->m_single;   // integers: one shape (the 256-thread kernel)
     if (o.low_cols) p->m_single = p->m_small = p->m_few = o.low_cols;
     if (shape.m_single >= 1 && shape.m_single <= kMaxLow && !o.low_cols) p->m_small = shape.m_single;
     if (shape.layer_threads == 384 || shape.layer_threads == 512 || shape.layer_threads == 768)
@@ -281,8 +283,9 @@ static perm_status plan_create_core(int n_max, perm_dtype dtype, const perm_opts
         sz_batched = p->sz_ws_per_cta * (size_t)p->sz_grid;
         // largest n whose single-matrix workspace fits the remaining budget
         for (int n = 1; n <= std::min(n_max, kMaxNSZ); n++) {
-            const size_t need = std::max(sz_matrix_workspace_bytes(dtype, n, layer_m(p, n)),
-                                         sz_matrix_workspace_bytes(dtype, n, layer_m(p, n, 1)));
+            size_t need = 0;
+            for (int c = 1; c <= kFlowMaxCount + 1; c++)
+                need = std::max(need, sz_matrix_workspace_bytes(dtype, n, layer_m(p, n, c)));
             if (need + (size_t)(1 << 20) <= p->budget) {
                 p->sz_single_nmax = n;
                 sz_single = std::max(sz_single, need);
@@ -373,13 +376,14 @@ int perm_plan_describe(perm_plan_t p, char* buf, size_t len) {
                     "\"sz_batch_nmax\": %d, \"sz_single_nmax\": %d, \"chain_width_batched\": %d, "
                     "\"chain_width_single\": %d, \"cta_threads\": %d, \"batched_grid\": %d, "
                     "\"layer_cta_threads\": %d, \"layer_ctas_per_sm\": %d, \"layer_small_nmax\": %d, "
-                    "\"chain_width_layer_few\": %d, "
+                    "\"chain_width_layer_few\": %d, \"chain_width_layer_few_n20\": %d, "
                     "\"chain_width_layer_small\": %d, \"layer_cta_threads_small\": %d, "
                     "\"layer_ctas_per_sm_small\": %d, "
                     "\"workspace_bytes\": %zu, \"out_words\": %d, \"autotuned\": %s}",
                     dt, p->n_max, p->method, p->flags, p->sz_batch_nmax, p->sz_single_nmax, p->m_low,
                     p->m_single, p->dtype == PERM_C128 ? p->c128_threads : p->int_threads, p->sz_grid,
-                    p->dtype == PERM_C128 ? p->layer_threads : 256, p->layer_grid_mult, kLayerSmallN, p->m_few,
+                    p->dtype == PERM_C128 ? p->layer_threads : 256, p->layer_grid_mult, kLayerSmallN,
+                    layer_m(p, kLayerSmallN, 1), layer_m(p, 20, 1),
                     p->m_small, p->dtype == PERM_C128 ? p->layer_threads_small : 256, p->layer_grid_small,
                     perm_plan_workspace_bytes(p), p->dtype == PERM_C128 ? 0 : p->out_words,
                     p->tuned ? "true" : "false");
@@ -906,8 +910,9 @@ static perm_status plan_create_tuned(int n_max, perm_dtype dtype, const perm_opt
                 else break;
             }
             best.shape.batch_nmax = cross;
-            // (3) the layer path's shape for orders up to kLayerSmallN, on four matrices of order nbig
-            // (one or two matrices take the narrower chains of m_few)
+            // (3) the layer path's shape for orders up to kLayerSmallN, on eight matrices of order
+            // nbig (at most kFlowMaxCount matrices take the dataflow launch, whose chain width
+            // follows the order and the count)
             const int cand[4][3] = {{384, 12, 2}, {384, 12, 4}, {512, 13, 1}, {512, 12, 2}};
             float lbest = 0.f;
             for (const auto& c : cand) {
@@ -915,7 +920,7 @@ static perm_status plan_create_tuned(int n_max, perm_dtype dtype, const perm_opt
                 sh.layer_threads = c[0];
                 sh.m_single = c[1];
                 sh.layer_grid_mult = c[2];
-                const float ms = time_shape(nbig, dtype, o, sh, nbig, dm, kLayerFewCount + 2, dout, st);
+                const float ms = time_shape(nbig, dtype, o, sh, nbig, dm, 2 * kFlowMaxCount, dout, st);
                 if (ms > 0.f && (lbest == 0.f || ms < lbest)) {
                     lbest = ms;
                     best.shape.layer_threads = c[0];

@@ -242,18 +242,32 @@ cudaError_t sz_launch_single(int dtype, const void* mats, long long offset, int 
 // or 768 (one); every choice gives the same bits.
 //
 // Default shape of the complex layer path by order and by the number of matrices of that order
-// in one launch (measured on GB300): up to order 24, chains of 2^12 entries at two 384-thread
-// CTAs per SM, since more and smaller chains fill the narrow first and last layers (one n = 24
-// matrix 2.08 ms against 2.56 ms with 2^13), and for one or two matrices chains of 2^11, whose
-// shorter chains shorten the critical path through the t + 1 layers (one n = 20 matrix 0.48 ms
-// against 0.63; n = 23 1.24 against 1.40); above order 24 chains of 2^13 at one 768-thread CTA
-// per SM, since one outer column fewer means fewer predecessor loads (n = 28 25.6 ms against
-// 32.3 ms, n = 32 447 ms against 572 ms).
+// in one launch (measured on GB300; every shape gives the same bits).
+// - Up to order 24 and more than kFlowMaxCount matrices: chains of 2^12 entries at two
+//   384-thread CTAs per SM. More and smaller chains fill the narrow first and last layers (one
+//   n = 24 matrix 2.08 ms against 2.56 ms with 2^13).
+// - Up to order 24 and at most kFlowMaxCount matrices (the dataflow launch): chains of
+//   2^w, w = floor((n - 1 + floor(log2 count)) / 2) clamped to 9..12. The critical path through
+//   the t + 1 layers is then what binds, and shorter chains shorten it until their predecessor
+//   loads dominate. This w was within 5 % of the best of 9..12 at n = 16..24 and 1, 2 or 4
+//   matrices: one n = 20 matrix 0.35 ms (0.43 with 2^11), four n = 18 matrices 0.30 ms (0.43
+//   with 2^12), one n = 24 matrix 1.83 ms with 2^11.
+// - Above order 24: chains of 2^13 at one 768-thread CTA per SM. One outer column fewer means
+//   fewer predecessor loads (n = 28 25.6 ms against 32.3 ms, n = 32 447 ms against 572 ms).
 constexpr int kLayerSmallN = 24;
-constexpr int kLayerFewCount = 2;
+constexpr int kFlowMaxCount = 4;   // the dataflow launch takes at most this many matrices of an order
 inline void sz_layer_default_shape(int n, int count, int* m, int* threads) {
-    *m = n > kLayerSmallN ? 13 : (count <= kLayerFewCount ? 11 : 12);
     *threads = n > kLayerSmallN ? 768 : 384;
+    if (n > kLayerSmallN) {
+        *m = 13;
+    } else if (count <= kFlowMaxCount) {
+        int lg = 0;
+        for (int c = count; c > 1; c >>= 1) lg++;
+        const int w = (n - 1 + lg) / 2;
+        *m = w < 9 ? 9 : (w > 12 ? 12 : w);
+    } else {
+        *m = 12;
+    }
 }
 cudaError_t sz_launch_layers(int dtype, const void* mats, const ItemDesc* items, int count, int n, int m,
                              void* out, int out_words, int* item_status, void* workspace,

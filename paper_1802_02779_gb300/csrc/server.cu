@@ -227,16 +227,19 @@ int table_low(int n, int count) {
     sz_layer_default_shape(n, count, &m, &threads);
     return m;
 }
-// Jobs of at most this many matrices of an order up to kLayerSmallN run as one dataflow launch.
-constexpr int kTableFlowMax = 4;
-bool table_flow(int n, int count) { return n <= kLayerSmallN && count <= kTableFlowMax; }
+// Jobs of at most kFlowMaxCount matrices of an order up to kLayerSmallN run as one dataflow launch.
+bool table_flow(int n, int count) { return n <= kLayerSmallN && count <= kFlowMaxCount; }
 size_t table_item_bytes(int n, int count) {
     const int m = table_low(n, count);
     return table_flow(n, count) ? sz_flow_workspace_bytes(n, m) : sz_matrix_workspace_bytes(PERM_C128, n, m);
 }
 size_t table_bytes(int n, int count) { return (size_t)count * table_item_bytes(n, count); }
 // The most one matrix of order n can take (admission to the table lane).
-size_t table_bytes_max(int n) { return std::max(table_item_bytes(n, 1), table_item_bytes(n, kLayerFewCount + 1)); }
+size_t table_bytes_max(int n) {
+    size_t b = 0;
+    for (int c = 1; c <= kFlowMaxCount + 1; c++) b = std::max(b, table_item_bytes(n, c));
+    return b;
+}
 
 // Work of one request on the Ryser lane in complex-code equivalents (the batch bound).
 double ryser_codes(const Request* r) {

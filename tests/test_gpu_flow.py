@@ -47,3 +47,23 @@ def test_flow_mixed_orders_in_one_call(lp, monkeypatch):
     for g, m in zip(got, mats):
         assert g == lp.permanents([m], "c128", method=lp.METHOD_SZ)[0]
     assert abs(got[1] - oracle_c(mats[1])) <= tol_c(mats[1])
+
+
+@pytest.mark.parametrize("count", [1, 2, 4])
+def test_flow_chain_width_by_order_and_count(lp, count):
+    """At most four matrices of an order up to 24 take chains of 2^w, w = floor((n - 1 +
+    floor(log2 count)) / 2) clamped to 9..12; the bits are those of any fixed width."""
+    with lp.Plan(24, "c128", method=lp.METHOD_SZ) as p:
+        d = p.describe()
+        assert d["chain_width_layer_few_n20"] == 9 and d["chain_width_layer_few"] == 11
+    for n in (12, 18, 23):
+        mats = [rand_complex(n, 13700 + 10 * n + i) for i in range(count)]
+        res = []
+        for low in (0, 12):
+            with lp.Plan(n, "c128", method=lp.METHOD_SZ, max_batch=count, low_cols=low) as p:
+                got, st = lp.permanents(mats, "c128", plan=p, return_status=True)
+            assert list(st) == [lp.PERM_OK] * count
+            res.append(list(got))
+        assert res[0] == res[1]
+        if n <= 18:
+            assert abs(res[0][0] - oracle_c(mats[0])) <= tol_c(mats[0])
