@@ -130,7 +130,11 @@ typedef struct perm_opts {
     int method;               /* perm_method */
     unsigned flags;           /* PERM_FLAG_* */
     int ctas_per_sm;          /* persistent CTAs per SM for batched launches; 0 = tuned */
-    int low_cols;             /* Store-zechin low-column count m, 1..13 (shared-memory chain width); 0 = 12 batched, 13 single */
+    int low_cols;             /* Store-zechin low-column count m, 1..13 (shared-memory chain width), for every
+                                 launch of the plan; 0 = the defaults: 12 for the batched kernel and for
+                                 more than four matrices of an order <= 24 per launch, 13 above order 24,
+                                 and for at most four matrices of an order n <= 24 (one dataflow launch)
+                                 floor((n - 1 + floor(log2 count)) / 2) clamped to 9..12 */
 } perm_opts;
 
 typedef struct perm_plan_s *perm_plan_t;
