@@ -516,7 +516,7 @@ perm_status enqueue(perm_plan_t p, const BatchLayout& L, const void* mats, const
             const int c = (int)std::min<long long>(per_launch, g.cnt - b0);
             if (flow)
                 e = sz_launch_flow(mats, dd + g.at + b0, c, g.n, lm, out, item_status, p->ws, ws_item,
-                                   p->d_counter + 1, 2 * p->num_sms, st);
+                                   p->d_counter + 1, p->num_sms, st);
             else
                 e = sz_launch_layers(p->dtype, mats, dd + g.at + b0, c, g.n, lm, out, p->out_words, item_status,
                                      p->ws, ws_item, (small ? p->layer_grid_small : p->layer_grid_mult) * p->num_sms,

@@ -279,11 +279,13 @@ cudaError_t sz_launch_layers(int dtype, const void* mats, const ItemDesc* items,
 // sz_launch_layers.  Matrix c uses [c * ws_bytes_per_item, ...) of the
 // workspace, ws_bytes_per_item >= sz_flow_workspace_bytes(n, m) (three layer
 // regions and the chains' done flags); *counter is zeroed here.  An item whose
-// wait gives up reports PERM_ETIMEDOUT in item_status.
+// wait gives up reports PERM_ETIMEDOUT in item_status.  The grid is persistent:
+// three 256-thread CTAs per SM for chains of up to 2^11 entries, else two of 384
+// threads, over num_sms SMs.
 size_t sz_flow_workspace_bytes(int n, int m);
 cudaError_t sz_launch_flow(const void* mats, const ItemDesc* items, int count, int n, int m, void* out,
                            int* item_status, void* workspace, size_t ws_bytes_per_item, unsigned* counter,
-                           int grid, cudaStream_t st);
+                           int num_sms, cudaStream_t st);
 
 // Ryser: every matrix's codes are cut into ryser_parts(dtype, n) CTA-sized
 // pieces (a function of n only).  One launch per distinct order n.  allow192:

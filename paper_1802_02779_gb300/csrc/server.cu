@@ -372,7 +372,7 @@ bool table_launch(perm_server_t s, Slot& S, std::vector<Request*>& job) {
     // most a chain's time for SMs, not a whole layer launch's
     if (ok && table_flow(n, c))
         ok = sz_launch_flow(S.d_in, S.d_desc, c, n, lm, S.d_out, S.d_status, ws, ws_item, S.d_counter,
-                            2 * s->num_sms, S.stream) == cudaSuccess;
+                            s->num_sms, S.stream) == cudaSuccess;
     else if (ok)
         ok = sz_launch_layers(PERM_C128, S.d_in, S.d_desc, c, n, lm, S.d_out, 2, S.d_status, ws, ws_item,
                               1 << 30, S.stream, lthreads) == cudaSuccess;

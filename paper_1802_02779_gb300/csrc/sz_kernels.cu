@@ -920,7 +920,8 @@ __host__ __device__ inline size_t flow_layer_words(int n, int m) {
     return (size_t)binom_calc(t, t / 2) * chain_words(kC128, m);
 }
 
-__global__ void __launch_bounds__(kThreadsFlow, 2)
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 3 : 2)
 sz_flow_c128(const double2* __restrict__ mats, const ItemDesc* __restrict__ items, int count, int n,
              int m_param, double2* out, int* item_status, unsigned long long* workspace,
              size_t ws_words_per_item, unsigned* counter) {
@@ -1300,10 +1301,15 @@ size_t sz_flow_workspace_bytes(int n, int m_param) {
 
 cudaError_t sz_launch_flow(const void* mats, const ItemDesc* items, int count, int n, int m, void* out,
                            int* item_status, void* workspace, size_t ws_bytes_per_item, unsigned* counter,
-                           int grid, cudaStream_t st) {
+                           int num_sms, cudaStream_t st) {
     if (count <= 0) return cudaSuccess;
     if (n > kLayerSmallN || ws_bytes_per_item < sz_flow_workspace_bytes(n, m)) return cudaErrorInvalidValue;
     const int mm = sz_low_for(n, m);
+    // chains of up to 2^11 entries: three 256-thread CTAs per SM (more chains in flight, and more
+    // entries per thread between barriers; measured on GB300: one n = 20 matrix 0.33 ms against
+    // 0.35, four n = 22 matrices 1.54 ms against 1.69); wider chains: two 384-thread CTAs
+    const int threads = mm <= 11 ? 256 : kThreadsFlow;
+    const int grid = (threads == 256 ? 3 : 2) * num_sms;
     const int t = n - mm;
     const size_t flag_off = 3 * flow_layer_words(n, mm) * 8;
     const size_t flag_bytes = (((size_t)1 << t) + t + 2) * sizeof(int);
@@ -1311,11 +1317,17 @@ cudaError_t sz_launch_flow(const void* mats, const ItemDesc* items, int count, i
                                       flag_bytes, (size_t)count, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(unsigned), st);
     const int smem = sz_smem_bytes(PERM_C128, n, m);
-    if (e == cudaSuccess) e = set_smem((const void*)sz_flow_c128, smem);
+    const void* fn = threads == 256 ? (const void*)sz_flow_c128<256> : (const void*)sz_flow_c128<kThreadsFlow>;
+    if (e == cudaSuccess) e = set_smem(fn, smem);
     if (e != cudaSuccess) return e;
-    sz_flow_c128<<<grid, kThreadsFlow, smem, st>>>((const double2*)mats, items, count, n, m, (double2*)out,
+    if (threads == 256)
+        sz_flow_c128<256><<<grid, 256, smem, st>>>((const double2*)mats, items, count, n, m, (double2*)out,
                                                    item_status, (unsigned long long*)workspace,
                                                    ws_bytes_per_item / 8, counter);
+    else
+        sz_flow_c128<kThreadsFlow><<<grid, kThreadsFlow, smem, st>>>(
+            (const double2*)mats, items, count, n, m, (double2*)out, item_status,
+            (unsigned long long*)workspace, ws_bytes_per_item / 8, counter);
     return cudaGetLastError();
 }
 
@@ -1335,7 +1347,7 @@ cudaError_t sz_launch_single(int dtype, const void* mats, long long offset, int 
 
 cudaError_t sz_preload(int dtype) {
     cudaFuncAttributes fa;
-    const void* fns[14];
+    const void* fns[16];
     int k = 0;
     fns[k++] = (const void*)trivial_kernel;
     if (dtype == PERM_C128) {
@@ -1345,7 +1357,8 @@ cudaError_t sz_preload(int dtype) {
         fns[k++] = c128_batched_fn(768);
         for (int threads : {384, 512, 768})
             for (bool compact : {false, true}) fns[k++] = (const void*)pick_c128_layer(threads, compact);
-        fns[k++] = (const void*)sz_flow_c128;
+        fns[k++] = (const void*)sz_flow_c128<kThreadsFlow>;
+        fns[k++] = (const void*)sz_flow_c128<256>;
     } else {
         for (int n_max : {20, 34})
             for (int threads : {256, 512}) fns[k++] = (const void*)pick_int_batched(dtype, n_max, threads);
