@@ -117,10 +117,10 @@ class Clocks:
 
 
 # DRAM bytes (read + write) per n = 20 complex matrix of sz_batched_c128, from the ncu capture
-# summarised in profiles/sz_batched_c128_n20.md (304 matrices: 29.766831 GB + 7.642462 GB).
+# summarised in profiles/sz_batched_c128_n20.md (304 matrices: 29.766018 GB + 7.642920 GB).
 # Valid only for the kernel source it was measured on; otherwise the bench reports null.
-TRAFFIC_C128_PER_MATRIX = (29.766831e9 + 7.642462e9) / 304
-TRAFFIC_SOURCE_SHA256 = "11c65476b0e1da6e35a45fe97a37085eb8f14fe79c84b21fd0fed650b227bfe5"
+TRAFFIC_C128_PER_MATRIX = (29.766018e9 + 7.642920e9) / 304
+TRAFFIC_SOURCE_SHA256 = "6bae25e5546f5c116f1a0761fe0cfad8f4beb31e333d40f41125b77b5e464648"
 
 
 def traffic_per_launch(count: int):
